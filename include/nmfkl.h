@@ -1,0 +1,195 @@
+/*
+ * nmfkl -- sparse randomized coordinate descent (SRCD) for nonnegative matrix
+ * factorization with KL divergence on one GB300 GPU (sm_103a).
+ *
+ * Method: Nguyen & Ho, "Fast parallel randomized algorithm for nonnegative
+ * matrix factorization with KL divergence for large sparse datasets".
+ *   Problem (Section 1, Eq. 1/2): V (n x m, sparse counts) ~= W^T F with
+ *   W (r x n) >= 0, F (r x m) >= 0, minimising
+ *     D(V || W^T F) + a1/2 |W|^2 + a2/2 |F|^2 + b1 |W|_1 + b2 |F|_1.
+ *   Algorithm 1 alternates a half over the m columns of F (W fixed) and a
+ *   half over the n rows of W (F fixed); the subproblems of a half are
+ *   independent (Eq. 3). Algorithm 2 solves one subproblem
+ *     min_{x >= 0} D(v || A x) + alpha/2 |x|^2 + beta |x|_1
+ *   by a projected Newton step per coordinate (Section 2) in a random order,
+ *   with the derivatives of Eq. Partial evaluated on the nonzeros of v only.
+ *
+ * Conventions for every entry point:
+ *   - Status: every call returns nmfkl_status; no C++ exception crosses this
+ *     boundary. On failure nmfkl_last_error(ctx) describes the cause.
+ *   - Ownership: the caller owns every pointer it passes. The library copies
+ *     what it keeps (device copies inside the context) and never frees or
+ *     retains caller memory after the call returns.
+ *   - mem_kind: 0 = the pointer is host memory, 1 = device memory of the
+ *     context's device.
+ *   - Layouts: W is r x n and F is r x m, row-major FP32 (the paper returns
+ *     W^T; this library keeps the r-major orientation of Algorithm 1's
+ *     "Randomize" lines). Sparse V is given as CSC (colptr int64[m+1],
+ *     rowidx int32[nnz], val float[nnz]) and CSR (rowptr int64[n+1],
+ *     colidx int32[nnz], rval float[nnz]), 0-based, indices strictly
+ *     increasing within a column (row), values finite and > 0.
+ *   - Streams: work is ordered on the stream given to nmfkl_create (0 = the
+ *     legacy default stream). Calls that return host values synchronize it.
+ *   - Precision: W, F, the model values x = [W^T F]_ij at the nonzeros and
+ *     the three per-coordinate sums run in FP32; the KL objective is
+ *     accumulated in FP64.
+ */
+#ifndef NMFKL_H
+#define NMFKL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NMFKL_OK = 0,
+    NMFKL_EINVAL = 1,    /* bad argument, size or input data */
+    NMFKL_ENOMEM = 2,    /* device or host allocation failed */
+    NMFKL_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    NMFKL_ENUMERIC = 4,  /* NaN or Inf in the objective */
+    NMFKL_ETIMEOUT = 5,  /* a bounded device wait gave up */
+    NMFKL_EBUSY = 6,     /* not admissible now (serving) */
+    NMFKL_ENOTCONV = 7   /* max_sweeps reached before the tolerance */
+} nmfkl_status;
+
+/* Parameters of Algorithms 1 and 2. nmfkl_default_params fills the defaults. */
+typedef struct {
+    int32_t r;            /* latent factors, 1 <= r <= 256 */
+    double alpha_W;       /* a1: L2 weight on W (Eq. 2) */
+    double beta_W;        /* b1: L1 weight on W */
+    double alpha_F;       /* a2: L2 weight on F */
+    double beta_F;        /* b2: L1 weight on F */
+    double eps_grad;      /* gradient tolerance of Algorithm 2's while test; default 1e-6 */
+    double eps_div;       /* added to [Ax]_i in every division and log (Algorithm 2's
+                             log([Ax]_i + eps)); default 1e-10 */
+    double eps_x;         /* relative step that ends a coordinate's Newton loop;
+                             default 0.1 (Section 3) */
+    int32_t max_inner;    /* cap on Newton steps per coordinate; default 16 */
+    int32_t grad_mode;    /* 0 (default): tolerance eps_grad*(sumA_k + beta) and the
+                             interior test x_k > 0; 1: the paper's absolute epsilon
+                             in both places */
+    int32_t break_mode;   /* 0 (default): break when |dx| < eps_x*xs; 1: the signed
+                             test dx < eps_x*xs as printed */
+    int32_t perm_mode;    /* 0 (default): coordinate order keyed by (seed, sweep, side,
+                             column); 1: one order per sweep shared by every column
+                             and row (Algorithm 1 draws ids once per iteration) */
+    uint64_t seed;        /* Philox4x64-10 key for coordinate orders and random init */
+} nmfkl_params;
+
+typedef struct nmfkl_ctx nmfkl_ctx;
+
+/* Work counters accumulated since the last reset (debug and roofline use). */
+typedef struct {
+    int64_t coords;    /* coordinates visited */
+    int64_t evals;     /* derivative evaluations (Eq. Partial passes over a subproblem) */
+    int64_t steps;     /* projected Newton steps */
+    int64_t cap_hits;  /* coordinates stopped by max_inner */
+} nmfkl_counters;
+
+/* Fills *p with the defaults listed above and the given r. */
+void nmfkl_default_params(nmfkl_params *p, int32_t r);
+
+/* Human-readable name of a status code (static storage). */
+const char *nmfkl_status_string(nmfkl_status s);
+
+/* Creates a context for an n x m problem on `device`, ordered on `stream`
+ * (a cudaStream_t, or NULL for the default stream). Allocates W and F on the
+ * device. EINVAL for r outside [1, 256], n < 1, m < 1. */
+nmfkl_status nmfkl_create(const nmfkl_params *p, int64_t n, int64_t m, int32_t device,
+                          void *stream, nmfkl_ctx **out);
+
+/* Releases every device allocation of the context. NULL is a no-op. */
+void nmfkl_destroy(nmfkl_ctx *ctx);
+
+/* Last error message of the context ("" if none). */
+const char *nmfkl_last_error(const nmfkl_ctx *ctx);
+
+/* Copies V into the context: CSC for the F half (Algorithm 1, columns V_j)
+ * and CSR for the W half (rows V_i^T). With mem_kind 0 the CSR arrays may be
+ * NULL and are built on the host. Host inputs are validated (EINVAL on an
+ * out-of-range or unsorted index, a non-finite or non-positive value, or
+ * inconsistent pointers). Plans the length buckets of both halves. */
+nmfkl_status nmfkl_set_data(nmfkl_ctx *ctx, int64_t nnz,
+                            const int64_t *colptr, const int32_t *rowidx, const float *val,
+                            const int64_t *rowptr, const int32_t *colidx, const float *rval,
+                            int32_t mem_kind);
+
+/* Sets the starting W (r x n) and F (r x m). A NULL pointer draws that
+ * factor from Uniform[0,1) with Philox4x64-10 (Algorithm 1, "Randomize"):
+ * entry e of the row-major matrix takes word e%4 of the block with counter
+ * (e/4, which, 0, 0), which = 0 for W and 1 for F, key (seed,
+ * 0x5352434400000002), as (word >> 40) * 2^-24. */
+nmfkl_status nmfkl_init(nmfkl_ctx *ctx, const float *W0, const float *F0, int32_t mem_kind);
+
+/* One F half of Algorithm 1 (sweep index `sweep`): sumW = W 1, then every
+ * column j of F is updated by Algorithm 2 on (V_j, W^T, sumW, F_j, a2, b2,
+ * ids(seed, sweep, side 0, j)). Asynchronous on the context stream. */
+nmfkl_status nmfkl_sweep_F(nmfkl_ctx *ctx, int64_t sweep);
+
+/* One W half of Algorithm 1: sumF = F 1, then every row i of W by Algorithm
+ * 2 on (V_i^T, F^T, sumF, W_i, a1, b1, ids(seed, sweep, side 1, i)).
+ * Asynchronous on the context stream. */
+nmfkl_status nmfkl_sweep_W(nmfkl_ctx *ctx, int64_t sweep);
+
+/* Eq. 1 at the current W, F into *kl (FP64 accumulation; zero entries of V
+ * contribute x_ij, summed in closed form as sumW . sumF) and the Eq. 2
+ * regularizer into *reg (either pointer may be NULL). Synchronizes.
+ * ENUMERIC if the value is not finite. */
+nmfkl_status nmfkl_objective(nmfkl_ctx *ctx, double *kl, double *reg);
+
+/* Algorithm 1 from the current state: sweeps s = sweep0, sweep0+1, ... (F
+ * half then W half) until |D_s - D_{s-1}| <= rel_tol * D_{s-1} or
+ * max_sweeps. kl_trace (host, max_sweeps doubles, may be NULL) receives
+ * Eq. 1 after each sweep; *sweeps_done (may be NULL) the count. Returns
+ * ENOTCONV when max_sweeps ran out first and rel_tol > 0. */
+nmfkl_status nmfkl_fit(nmfkl_ctx *ctx, int64_t sweep0, int32_t max_sweeps, double rel_tol,
+                       double *kl_trace, int32_t *sweeps_done);
+
+/* One full pass of the hot path: nmfkl_sweep_F(sweep), nmfkl_sweep_W(sweep),
+ * then Eq. 1 into *kl (may be NULL) for Algorithm 1's convergence test.
+ * Synchronizes (the objective is read back). */
+nmfkl_status nmfkl_step(nmfkl_ctx *ctx, int64_t sweep, double *kl);
+
+/* Copies W (r x n) or F (r x m), row-major FP32, to host or device memory. */
+nmfkl_status nmfkl_get_W(nmfkl_ctx *ctx, float *out, int32_t mem_kind);
+nmfkl_status nmfkl_get_F(nmfkl_ctx *ctx, float *out, int32_t mem_kind);
+
+/* Reads and resets (reset != 0) the work counters. Synchronizes. */
+nmfkl_status nmfkl_get_counters(nmfkl_ctx *ctx, nmfkl_counters *out, int32_t reset);
+
+/* Kernel timing: with enable != 0 every kernel the library launches is
+ * bracketed by CUDA events on the context stream. nmfkl_kernel_times
+ * synchronizes and returns, for up to `cap` kernel families, the family
+ * name (static storage), launch count and summed milliseconds; the return
+ * value is the number of families. reset != 0 clears them. */
+nmfkl_status nmfkl_set_timing(nmfkl_ctx *ctx, int32_t enable);
+int32_t nmfkl_kernel_times(nmfkl_ctx *ctx, const char **names, int64_t *launches, double *ms,
+                           int32_t cap, int32_t reset);
+
+/* Launch plan of the sweep kernels: one entry per length bucket and half. */
+typedef struct {
+    const char *kernel;  /* kernel family name (static storage) */
+    int32_t side;        /* 0 = F half (columns), 1 = W half (rows) */
+    int32_t count;       /* units in the bucket */
+    int64_t nnz;         /* nonzeros of those units */
+    int64_t max_len;     /* longest unit */
+    int32_t grid, block; /* persistent launch shape */
+    int64_t smem;        /* dynamic shared memory per block, bytes */
+} nmfkl_bucket_info;
+
+/* Fills up to `cap` entries; returns the number of buckets (-1 on a NULL ctx). */
+int32_t nmfkl_plan_info(const nmfkl_ctx *ctx, nmfkl_bucket_info *out, int32_t cap);
+
+/* Coordinate orders exactly as the sweep kernels draw them, computed on the
+ * device: out[c*r + t] = ids_t of unit cols[c] (device int32 arrays).
+ * side 0 = F half, 1 = W half. Synchronizes. */
+nmfkl_status nmfkl_debug_perm(nmfkl_ctx *ctx, int64_t sweep, int32_t side, int64_t count,
+                              const int64_t *cols, int32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMFKL_H */

@@ -1,0 +1,213 @@
+"""SRCD for NMF with KL divergence on one GB300 GPU.
+
+A thin Python binding over the C ABI of ``libnmfkl.so`` (``include/nmfkl.h``).
+The binding only marshals arguments: every step of a sweep runs in the
+library's CUDA kernels. PyTorch, when used, only provides device memory
+(``tensor.data_ptr()``) and streams.
+
+    import paper_1604_04026_gb300 as nk
+    V = nk.synth.docs(30000, 100000, 50)
+    model = nk.NMFKL(V.n, V.m, r=50)
+    model.set_data(V)
+    model.init()                      # Uniform[0,1) from the seed
+    trace, done = model.fit(20)       # Algorithm 1, KL after each sweep
+    W, F = model.get_W(), model.get_F()
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native, synth
+from ._native import Counters, Params
+
+__all__ = ["NMFKL", "NMFKLError", "Params", "default_params", "synth"]
+
+
+class NMFKLError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.status_name = _native.STATUS_NAMES.get(status, str(status))
+        super().__init__("%s: %s" % (self.status_name, message))
+
+
+def default_params(r: int, **kw) -> Params:
+    p = Params()
+    _native.load().nmfkl_default_params(ctypes.byref(p), r)
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError("unknown parameter %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, mem_kind, keepalive) for a numpy array or a torch tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        want = {np.float32: "torch.float32", np.int32: "torch.int32", np.int64: "torch.int64"}[dtype]
+        if str(x.dtype) != want:
+            raise TypeError("expected %s, got %s" % (want, x.dtype))
+        return x.data_ptr(), (1 if x.is_cuda else 0), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, 0, a
+
+
+class NMFKL:
+    """One factorization problem V (n x m) ~= W^T F with W (r x n), F (r x m)."""
+
+    def __init__(self, n: int, m: int, r: int | None = None, params: Params | None = None,
+                 device: int = 0, stream: int | None = None, **kw):
+        self._lib = _native.load()
+        if params is None:
+            if r is None:
+                raise ValueError("give r or params")
+            params = default_params(r, **kw)
+        self.params = params
+        self.n, self.m, self.r = int(n), int(m), int(params.r)
+        h = ctypes.c_void_p()
+        st = self._lib.nmfkl_create(ctypes.byref(params), self.n, self.m, device,
+                                    ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != 0:
+            raise NMFKLError(st, "nmfkl_create failed")
+        self._h = h
+
+    # -- plumbing
+    def _check(self, st: int, what: str):
+        if st != 0:
+            msg = self._lib.nmfkl_last_error(self._h)
+            raise NMFKLError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.nmfkl_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    # -- data and state
+    def set_data(self, V=None, *, nnz=None, colptr=None, rowidx=None, val=None, rowptr=None,
+                 colidx=None, rval=None):
+        """V: a synth.CountMatrix (host), or the six arrays (numpy or torch CUDA tensors)."""
+        if V is not None:
+            colptr, rowidx, val = V.colptr, V.rowidx, V.val
+            rowptr, colidx, rval = V.rowptr, V.colidx, V.rval
+            nnz = V.nnz
+        p = [_ptr(colptr, np.int64), _ptr(rowidx, np.int32), _ptr(val, np.float32),
+             _ptr(rowptr, np.int64), _ptr(colidx, np.int32), _ptr(rval, np.float32)]
+        kinds = {k for _, k, _ in p if _ is not None}
+        if len(kinds) > 1:
+            raise ValueError("mix of host and device arrays")
+        kind = kinds.pop() if kinds else 0
+        if nnz is None:
+            nnz = int(rowidx.shape[0])
+        self._check(self._lib.nmfkl_set_data(self._h, int(nnz), *[x[0] for x in p], kind), "set_data")
+
+    def init(self, W0=None, F0=None):
+        """Starting W (r x n) and F (r x m); None draws Uniform[0,1) from the seed."""
+        pw, kw, a = _ptr(W0, np.float32)
+        pf, kf, b = _ptr(F0, np.float32)
+        if W0 is not None and F0 is not None and kw != kf:
+            raise ValueError("W0 and F0 must both be host or both device")
+        kind = kw if W0 is not None else kf
+        self._check(self._lib.nmfkl_init(self._h, pw, pf, kind), "init")
+
+    def sweep_F(self, sweep: int):
+        self._check(self._lib.nmfkl_sweep_F(self._h, int(sweep)), "sweep_F")
+
+    def sweep_W(self, sweep: int):
+        self._check(self._lib.nmfkl_sweep_W(self._h, int(sweep)), "sweep_W")
+
+    def sweep(self, sweep: int):
+        self.sweep_F(sweep)
+        self.sweep_W(sweep)
+
+    def objective(self):
+        """(Eq. 1 value, Eq. 2 regularizer) in FP64."""
+        kl, reg = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.nmfkl_objective(self._h, ctypes.byref(kl), ctypes.byref(reg)), "objective")
+        return kl.value, reg.value
+
+    def fit(self, max_sweeps: int, rel_tol: float = 0.0, sweep0: int = 0, raise_notconv: bool = False):
+        """Algorithm 1; returns (KL after each sweep, sweeps done)."""
+        trace = np.zeros(max(max_sweeps, 1), dtype=np.float64)
+        done = ctypes.c_int32()
+        st = self._lib.nmfkl_fit(self._h, sweep0, max_sweeps, rel_tol, trace.ctypes.data, ctypes.byref(done))
+        if st != 0 and not (st == 7 and not raise_notconv):
+            self._check(st, "fit")
+        return trace[:done.value], done.value
+
+    def step(self, sweep: int) -> float:
+        """F half, W half and the objective (the whole hot path); returns Eq. 1."""
+        kl = ctypes.c_double()
+        self._check(self._lib.nmfkl_step(self._h, int(sweep), ctypes.byref(kl)), "step")
+        return kl.value
+
+    def plan(self) -> list:
+        """Launch plan: one dict per (half, length bucket)."""
+        cap = 64
+        arr = (_native.BucketInfo * cap)()
+        nb = self._lib.nmfkl_plan_info(self._h, arr, cap)
+        return [{"kernel": arr[i].kernel.decode(), "side": arr[i].side, "count": arr[i].count,
+                 "nnz": arr[i].nnz, "max_len": arr[i].max_len, "grid": arr[i].grid,
+                 "block": arr[i].block, "smem": arr[i].smem} for i in range(min(nb, cap))]
+
+    def _get(self, fn, rows, cols, out):
+        if out is None:
+            out = np.empty((rows, cols), dtype=np.float32)
+        p, kind, keep = _ptr(out, np.float32)
+        if kind == 0 and not isinstance(out, np.ndarray):
+            raise TypeError("host output must be a numpy array")
+        self._check(fn(self._h, p, kind), "get")
+        return out
+
+    def get_W(self, out=None):
+        """W (r x n); out may be a numpy array or a CUDA tensor."""
+        return self._get(self._lib.nmfkl_get_W, self.r, self.n, out)
+
+    def get_F(self, out=None):
+        """F (r x m); out may be a numpy array or a CUDA tensor."""
+        return self._get(self._lib.nmfkl_get_F, self.r, self.m, out)
+
+    def counters(self, reset: bool = False) -> dict:
+        c = Counters()
+        self._check(self._lib.nmfkl_get_counters(self._h, ctypes.byref(c), int(reset)), "counters")
+        return {k: int(getattr(c, k)) for k, _ in Counters._fields_}
+
+    def set_timing(self, enable: bool = True):
+        self._check(self._lib.nmfkl_set_timing(self._h, int(enable)), "set_timing")
+
+    def kernel_times(self, reset: bool = False) -> dict:
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_double * cap)()
+        nf = self._lib.nmfkl_kernel_times(self._h, names, launches, ms, cap, int(reset))
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(nf, cap))}
+
+    def debug_perm(self, sweep: int, side: int, cols_dev, out_dev):
+        """Device orders: out_dev[c, :] = ids of unit cols_dev[c] (CUDA tensors)."""
+        self._check(self._lib.nmfkl_debug_perm(self._h, sweep, side, int(cols_dev.numel()),
+                                               cols_dev.data_ptr(), out_dev.data_ptr()), "debug_perm")

@@ -1,0 +1,534 @@
+// C-ABI entry points of libnmfkl (declared in include/nmfkl.h).
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <thread>
+
+namespace nmfkl {
+
+int64_t dpart_required(int ldr);
+
+bool cuda_ok(nmfkl_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return true;
+    if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return false;
+}
+
+int timer_begin(nmfkl_ctx *c, const char *name) {
+    if (!c->timing) return -1;
+    int idx = -1;
+    for (size_t i = 0; i < c->timers.size(); ++i)
+        if (std::strcmp(c->timers[i].name, name) == 0) idx = (int)i;
+    if (idx < 0) {
+        c->timers.push_back(KernelTimer{name, 0, 0.0});
+        idx = (int)c->timers.size() - 1;
+    }
+    cudaEvent_t a, b;
+    if (!c->ev_pool.empty()) {
+        a = c->ev_pool.back();
+        c->ev_pool.pop_back();
+    } else {
+        cudaEventCreate(&a);
+    }
+    if (!c->ev_pool.empty()) {
+        b = c->ev_pool.back();
+        c->ev_pool.pop_back();
+    } else {
+        cudaEventCreate(&b);
+    }
+    cudaEventRecord(a, c->stream);
+    c->pending.push_back({idx, a, b});
+    return (int)c->pending.size() - 1;
+}
+
+void timer_end(nmfkl_ctx *c, int token) {
+    if (token < 0) return;
+    cudaEventRecord(c->pending[token].b, c->stream);
+}
+
+}  // namespace nmfkl
+
+using namespace nmfkl;
+
+namespace {
+
+template <class T>
+bool dev_alloc(nmfkl_ctx *c, T **p, int64_t count, const char *what) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) {
+        c->err = std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e);
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+void free_data(nmfkl_ctx *c) {
+    cudaFree(c->colptr); cudaFree(c->rowptr); cudaFree(c->rowidx); cudaFree(c->colidx);
+    cudaFree(c->val); cudaFree(c->rval); cudaFree(c->scratch);
+    c->colptr = c->rowptr = nullptr;
+    c->rowidx = c->colidx = nullptr;
+    c->val = c->rval = nullptr;
+    c->scratch = nullptr;
+    c->scratch_floats = 0;
+    free_plan(c);
+    c->have_data = false;
+}
+
+// Host-side check of one compressed layout, split over threads by unit range.
+// Returns 0 if valid, else 1 (offsets), 2 (indices), 4 (values).
+int check_range(int64_t u0, int64_t u1, int64_t extent, const int64_t *ptr, const int32_t *idx,
+                const float *val) {
+    for (int64_t u = u0; u < u1; ++u) {
+        if (ptr[u + 1] < ptr[u]) return 1;
+        int64_t prev = -1;
+        for (int64_t p = ptr[u]; p < ptr[u + 1]; ++p) {
+            if (idx[p] <= prev || idx[p] >= extent) return 2;
+            prev = idx[p];
+            if (!(val[p] > 0.f) || !std::isfinite(val[p])) return 4;
+        }
+    }
+    return 0;
+}
+
+bool check_host(nmfkl_ctx *c, int64_t units, int64_t extent, int64_t nnz, const int64_t *ptr,
+                const int32_t *idx, const float *val, const char *what) {
+    if (ptr[0] != 0 || ptr[units] != nnz) {
+        c->err = std::string(what) + ": offsets must start at 0 and end at nnz";
+        return false;
+    }
+    // offsets must be monotone before any thread indexes with them
+    for (int64_t u = 0; u < units; ++u)
+        if (ptr[u + 1] < ptr[u] || ptr[u + 1] > nnz) {
+            c->err = std::string(what) + ": offsets decrease or exceed nnz";
+            return false;
+        }
+    int nt = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 32);
+    if (nnz < (1 << 20)) nt = 1;
+    std::vector<int> res(nt, 0);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t] { res[t] = check_range(units * t / nt, units * (t + 1) / nt, extent, ptr, idx, val); });
+    for (auto &x : th) x.join();
+    int bad = 0;
+    for (int v : res) bad |= v;
+    if (bad & 2) c->err = std::string(what) + ": index out of range or not strictly increasing";
+    else if (bad & 4) c->err = std::string(what) + ": values must be finite and > 0";
+    else if (bad) c->err = std::string(what) + ": offsets decrease";
+    return bad == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nmfkl_default_params(nmfkl_params *p, int32_t r) {
+    std::memset(p, 0, sizeof(*p));
+    p->r = r;
+    p->eps_grad = 1e-6;
+    p->eps_div = 1e-10;
+    p->eps_x = 0.1;
+    p->max_inner = 16;
+    p->seed = 0;
+}
+
+const char *nmfkl_status_string(nmfkl_status s) {
+    switch (s) {
+        case NMFKL_OK: return "ok";
+        case NMFKL_EINVAL: return "invalid argument";
+        case NMFKL_ENOMEM: return "out of memory";
+        case NMFKL_ECUDA: return "CUDA error";
+        case NMFKL_ENUMERIC: return "non-finite objective";
+        case NMFKL_ETIMEOUT: return "device wait timed out";
+        case NMFKL_EBUSY: return "busy";
+        case NMFKL_ENOTCONV: return "not converged";
+    }
+    return "unknown status";
+}
+
+nmfkl_status nmfkl_create(const nmfkl_params *p, int64_t n, int64_t m, int32_t device, void *stream,
+                          nmfkl_ctx **out) {
+    if (!out) return NMFKL_EINVAL;
+    *out = nullptr;
+    if (!p || p->r < 1 || p->r > kMaxR || n < 1 || m < 1 || n > INT32_MAX || m > INT32_MAX ||
+        !(p->eps_x >= 0) || p->max_inner < 0 || !(p->eps_div >= 0) || !(p->eps_grad >= 0) ||
+        p->alpha_W < 0 || p->alpha_F < 0 || p->beta_W < 0 || p->beta_F < 0)
+        return NMFKL_EINVAL;
+    nmfkl_ctx *c = new (std::nothrow) nmfkl_ctx();
+    if (!c) return NMFKL_ENOMEM;
+    c->p = *p;
+    c->n = n;
+    c->m = m;
+    c->ldr = (p->r + 3) / 4 * 4;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (!cuda_ok(c, cudaSetDevice(device), "cudaSetDevice") ||
+        !cuda_ok(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count")) {
+        delete c;
+        return NMFKL_ECUDA;
+    }
+    c->dpart_len = dpart_required(c->ldr);
+    bool ok = dev_alloc(c, &c->Wt, n * c->ldr, "W") && dev_alloc(c, &c->Ft, m * c->ldr, "F") &&
+              dev_alloc(c, &c->sumW, c->ldr, "sumW") && dev_alloc(c, &c->sumF, c->ldr, "sumF") &&
+              dev_alloc(c, &c->dpart, c->dpart_len, "partials") && dev_alloc(c, &c->dscalar, 8, "scalars") &&
+              dev_alloc(c, &c->counters, 8, "counters") && dev_alloc(c, &c->queues, 64, "queues") &&
+              dev_alloc(c, &c->err_flag, 1, "error flag");
+    if (!ok) {
+        nmfkl_destroy(c);
+        return NMFKL_ENOMEM;
+    }
+    if (!cuda_ok(c, cudaMemset(c->Wt, 0, sizeof(float) * n * c->ldr), "zero W") ||
+        !cuda_ok(c, cudaMemset(c->Ft, 0, sizeof(float) * m * c->ldr), "zero F") ||
+        !cuda_ok(c, cudaMemset(c->counters, 0, sizeof(unsigned long long) * 8), "zero counters") ||
+        !cuda_ok(c, cudaMemset(c->err_flag, 0, sizeof(int32_t)), "zero flag")) {
+        nmfkl_destroy(c);
+        return NMFKL_ECUDA;
+    }
+    *out = c;
+    return NMFKL_OK;
+}
+
+void nmfkl_destroy(nmfkl_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_data(c);
+    cudaFree(c->Wt); cudaFree(c->Ft); cudaFree(c->sumW); cudaFree(c->sumF); cudaFree(c->dpart);
+    cudaFree(c->dscalar); cudaFree(c->counters); cudaFree(c->queues); cudaFree(c->err_flag);
+    cudaFree(c->tbuf);
+    for (auto &pd : c->pending) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+const char *nmfkl_last_error(const nmfkl_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+nmfkl_status nmfkl_set_data(nmfkl_ctx *c, int64_t nnz, const int64_t *colptr, const int32_t *rowidx,
+                            const float *val, const int64_t *rowptr, const int32_t *colidx, const float *rval,
+                            int32_t mem_kind) {
+    if (!c) return NMFKL_EINVAL;
+    if (nnz < 0 || nnz > INT32_MAX * 8LL || !colptr || (nnz > 0 && (!rowidx || !val)) ||
+        (mem_kind != 0 && mem_kind != 1)) {
+        c->err = "set_data: bad arguments";
+        return NMFKL_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    free_data(c);
+    const int64_t n = c->n, m = c->m;
+    std::vector<int64_t> h_rowptr;
+    std::vector<int32_t> h_colidx;
+    std::vector<float> h_rval;
+    if (mem_kind == 0) {
+        if (!check_host(c, m, n, nnz, colptr, rowidx, val, "CSC")) return NMFKL_EINVAL;
+        if (!rowptr) {
+            // CSR by a counting sort of the CSC (order within rows stays sorted)
+            h_rowptr.assign(n + 1, 0);
+            h_colidx.resize(nnz);
+            h_rval.resize(nnz);
+            for (int64_t p = 0; p < nnz; ++p) h_rowptr[rowidx[p] + 1]++;
+            for (int64_t i = 0; i < n; ++i) h_rowptr[i + 1] += h_rowptr[i];
+            std::vector<int64_t> fill(h_rowptr.begin(), h_rowptr.end() - 1);
+            for (int64_t j = 0; j < m; ++j)
+                for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+                    const int64_t q = fill[rowidx[p]]++;
+                    h_colidx[q] = (int32_t)j;
+                    h_rval[q] = val[p];
+                }
+            rowptr = h_rowptr.data();
+            colidx = h_colidx.data();
+            rval = h_rval.data();
+        } else if (!check_host(c, n, m, nnz, rowptr, colidx, rval, "CSR")) {
+            return NMFKL_EINVAL;
+        }
+    } else if (!rowptr || (nnz > 0 && (!colidx || !rval))) {
+        c->err = "set_data: device inputs need both CSC and CSR";
+        return NMFKL_EINVAL;
+    }
+    bool ok = dev_alloc(c, &c->colptr, m + 1, "colptr") && dev_alloc(c, &c->rowidx, nnz, "rowidx") &&
+              dev_alloc(c, &c->val, nnz, "val") && dev_alloc(c, &c->rowptr, n + 1, "rowptr") &&
+              dev_alloc(c, &c->colidx, nnz, "colidx") && dev_alloc(c, &c->rval, nnz, "rval");
+    if (!ok) {
+        free_data(c);
+        return NMFKL_ENOMEM;
+    }
+    const cudaMemcpyKind kind = mem_kind == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    ok = cuda_ok(c, cudaMemcpy(c->colptr, colptr, 8 * (m + 1), kind), "copy colptr") &&
+         cuda_ok(c, cudaMemcpy(c->rowptr, rowptr, 8 * (n + 1), kind), "copy rowptr");
+    if (ok && nnz > 0)
+        ok = cuda_ok(c, cudaMemcpy(c->rowidx, rowidx, 4 * nnz, kind), "copy rowidx") &&
+             cuda_ok(c, cudaMemcpy(c->val, val, 4 * nnz, kind), "copy val") &&
+             cuda_ok(c, cudaMemcpy(c->colidx, colidx, 4 * nnz, kind), "copy colidx") &&
+             cuda_ok(c, cudaMemcpy(c->rval, rval, 4 * nnz, kind), "copy rval");
+    if (!ok) {
+        free_data(c);
+        return NMFKL_ECUDA;
+    }
+    c->nnz = nnz;
+    if (mem_kind == 1) {
+        // device inputs: validate on the device
+        int32_t *flag = c->err_flag;
+        int32_t h = 0;
+        ok = cuda_ok(c, cudaMemsetAsync(flag, 0, 4, c->stream), "flag") &&
+             launch_validate(c, m, n, c->colptr, c->rowidx, c->val, flag) == NMFKL_OK &&
+             launch_validate(c, n, m, c->rowptr, c->colidx, c->rval, flag) == NMFKL_OK &&
+             cuda_ok(c, cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, c->stream), "flag copy") &&
+             cuda_ok(c, cudaStreamSynchronize(c->stream), "validate sync");
+        if (!ok) {
+            free_data(c);
+            return NMFKL_ECUDA;
+        }
+        int64_t last[2] = {0, 0};
+        cudaMemcpy(&last[0], c->colptr + m, 8, cudaMemcpyDeviceToHost);
+        cudaMemcpy(&last[1], c->rowptr + n, 8, cudaMemcpyDeviceToHost);
+        cudaMemsetAsync(flag, 0, 4, c->stream);
+        if (h != 0 || last[0] != nnz || last[1] != nnz) {
+            c->err = "set_data: device input failed validation (offsets, sorted in-range indices, values > 0)";
+            free_data(c);
+            return NMFKL_EINVAL;
+        }
+    }
+    nmfkl_status st = plan_side(c, 0);
+    if (st == NMFKL_OK) st = plan_side(c, 1);
+    if (st != NMFKL_OK) {
+        free_data(c);
+        return st;
+    }
+    if (c->scratch_floats > 0 && !dev_alloc(c, &c->scratch, c->scratch_floats, "scratch")) {
+        free_data(c);
+        return NMFKL_ENOMEM;
+    }
+    c->have_data = true;
+    return NMFKL_OK;
+}
+
+nmfkl_status nmfkl_init(nmfkl_ctx *c, const float *W0, const float *F0, int32_t mem_kind) {
+    if (!c || (mem_kind != 0 && mem_kind != 1)) return NMFKL_EINVAL;
+    cudaSetDevice(c->device);
+    const int64_t need = std::max(c->n, c->m) * (int64_t)c->p.r;
+    if (c->tbuf_floats < need) {
+        cudaFree(c->tbuf);
+        c->tbuf = nullptr;
+        c->tbuf_floats = 0;
+        if (!dev_alloc(c, &c->tbuf, need, "transpose buffer")) return NMFKL_ENOMEM;
+        c->tbuf_floats = need;
+    }
+    struct Item { const float *src; float *dst; int64_t cols; int which; } items[2] = {
+        {W0, c->Wt, c->n, 0}, {F0, c->Ft, c->m, 1}};
+    for (auto &it : items) {
+        nmfkl_status st;
+        if (!it.src) {
+            st = launch_uniform_init(c, it.which, it.dst, it.cols);
+        } else {
+            const float *src = it.src;
+            if (mem_kind == 0) {
+                if (!cuda_ok(c, cudaMemcpyAsync(c->tbuf, it.src, sizeof(float) * it.cols * c->p.r,
+                                                cudaMemcpyHostToDevice, c->stream), "copy init"))
+                    return NMFKL_ECUDA;
+                src = c->tbuf;
+            }
+            st = launch_to_unit_major(c, src, it.dst, it.cols);
+            if (st == NMFKL_OK && mem_kind == 0 &&
+                !cuda_ok(c, cudaStreamSynchronize(c->stream), "init sync"))
+                st = NMFKL_ECUDA;
+        }
+        if (st != NMFKL_OK) return st;
+    }
+    return NMFKL_OK;
+}
+
+static nmfkl_status sweep_side(nmfkl_ctx *c, int side, int64_t sweep) {
+    if (!c) return NMFKL_EINVAL;
+    if (!c->have_data) {
+        c->err = "no data: call nmfkl_set_data first";
+        return NMFKL_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    return run_half(c, side, sweep);
+}
+
+nmfkl_status nmfkl_sweep_F(nmfkl_ctx *c, int64_t sweep) { return sweep_side(c, 0, sweep); }
+nmfkl_status nmfkl_sweep_W(nmfkl_ctx *c, int64_t sweep) { return sweep_side(c, 1, sweep); }
+
+nmfkl_status nmfkl_objective(nmfkl_ctx *c, double *kl, double *reg) {
+    if (!c) return NMFKL_EINVAL;
+    if (!c->have_data) {
+        c->err = "no data: call nmfkl_set_data first";
+        return NMFKL_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    return launch_objective(c, kl, reg);
+}
+
+nmfkl_status nmfkl_fit(nmfkl_ctx *c, int64_t sweep0, int32_t max_sweeps, double rel_tol, double *kl_trace,
+                       int32_t *sweeps_done) {
+    if (!c || max_sweeps < 0 || !(rel_tol >= 0)) return NMFKL_EINVAL;
+    if (!c->have_data) {
+        c->err = "no data: call nmfkl_set_data first";
+        return NMFKL_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    double prev = 0.0;
+    nmfkl_status st = launch_objective(c, &prev, nullptr);
+    if (st != NMFKL_OK) return st;
+    int32_t s = 0;
+    bool conv = false;
+    while (s < max_sweeps) {
+        st = run_half(c, 0, sweep0 + s);
+        if (st == NMFKL_OK) st = run_half(c, 1, sweep0 + s);
+        double kl = 0.0;
+        if (st == NMFKL_OK) st = launch_objective(c, &kl, nullptr);
+        if (st != NMFKL_OK) {
+            if (sweeps_done) *sweeps_done = s;
+            return st;
+        }
+        if (kl_trace) kl_trace[s] = kl;
+        ++s;
+        if (rel_tol > 0 && std::fabs(prev - kl) <= rel_tol * std::fabs(prev)) {
+            conv = true;
+            break;
+        }
+        prev = kl;
+    }
+    if (sweeps_done) *sweeps_done = s;
+    int32_t flag = 0;
+    cudaMemcpy(&flag, c->err_flag, 4, cudaMemcpyDeviceToHost);
+    if (flag) {
+        c->err = "NaN produced in a sweep";
+        return NMFKL_ENUMERIC;
+    }
+    return (rel_tol > 0 && !conv) ? NMFKL_ENOTCONV : NMFKL_OK;
+}
+
+nmfkl_status nmfkl_step(nmfkl_ctx *c, int64_t sweep, double *kl) {
+    if (!c) return NMFKL_EINVAL;
+    if (!c->have_data) {
+        c->err = "no data: call nmfkl_set_data first";
+        return NMFKL_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    nmfkl_status st = run_half(c, 0, sweep);
+    if (st == NMFKL_OK) st = run_half(c, 1, sweep);
+    if (st == NMFKL_OK) st = launch_objective(c, kl, nullptr);
+    return st;
+}
+
+int32_t nmfkl_plan_info(const nmfkl_ctx *c, nmfkl_bucket_info *out, int32_t cap) {
+    if (!c) return -1;
+    int32_t i = 0;
+    for (int side = 0; side < 2; ++side)
+        for (const auto &b : c->plan[side]) {
+            if (out && i < cap) {
+                out[i].kernel = kind_name(b.kind);
+                out[i].side = side;
+                out[i].count = b.count;
+                out[i].nnz = b.nnz;
+                out[i].max_len = b.max_len;
+                out[i].grid = b.grid;
+                out[i].block = b.block;
+                out[i].smem = (int64_t)b.smem;
+            }
+            ++i;
+        }
+    return i;
+}
+
+static nmfkl_status get_factor(nmfkl_ctx *c, const float *Xt, int64_t cols, float *out, int32_t mem_kind) {
+    if (!c || !out || (mem_kind != 0 && mem_kind != 1)) return NMFKL_EINVAL;
+    cudaSetDevice(c->device);
+    const int64_t need = cols * (int64_t)c->p.r;
+    float *dst = out;
+    if (mem_kind == 0) {
+        if (c->tbuf_floats < need) {
+            cudaFree(c->tbuf);
+            c->tbuf = nullptr;
+            c->tbuf_floats = 0;
+            if (!dev_alloc(c, &c->tbuf, need, "transpose buffer")) return NMFKL_ENOMEM;
+            c->tbuf_floats = need;
+        }
+        dst = c->tbuf;
+    }
+    nmfkl_status st = launch_from_unit_major(c, Xt, dst, cols);
+    if (st != NMFKL_OK) return st;
+    if (mem_kind == 0) {
+        if (!cuda_ok(c, cudaMemcpyAsync(out, c->tbuf, sizeof(float) * need, cudaMemcpyDeviceToHost, c->stream),
+                     "copy factor"))
+            return NMFKL_ECUDA;
+        if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "get sync")) return NMFKL_ECUDA;
+    }
+    return NMFKL_OK;
+}
+
+nmfkl_status nmfkl_get_W(nmfkl_ctx *c, float *out, int32_t mem_kind) {
+    return c ? get_factor(c, c->Wt, c->n, out, mem_kind) : NMFKL_EINVAL;
+}
+nmfkl_status nmfkl_get_F(nmfkl_ctx *c, float *out, int32_t mem_kind) {
+    return c ? get_factor(c, c->Ft, c->m, out, mem_kind) : NMFKL_EINVAL;
+}
+
+nmfkl_status nmfkl_get_counters(nmfkl_ctx *c, nmfkl_counters *out, int32_t reset) {
+    if (!c || !out) return NMFKL_EINVAL;
+    cudaSetDevice(c->device);
+    unsigned long long h[4];
+    if (!cuda_ok(c, cudaMemcpyAsync(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "counters") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "counters sync"))
+        return NMFKL_ECUDA;
+    out->coords = (int64_t)h[0];
+    out->evals = (int64_t)h[1];
+    out->steps = (int64_t)h[2];
+    out->cap_hits = (int64_t)h[3];
+    if (reset && !cuda_ok(c, cudaMemsetAsync(c->counters, 0, sizeof(h), c->stream), "reset counters"))
+        return NMFKL_ECUDA;
+    return NMFKL_OK;
+}
+
+nmfkl_status nmfkl_set_timing(nmfkl_ctx *c, int32_t enable) {
+    if (!c) return NMFKL_EINVAL;
+    c->timing = enable != 0;
+    return NMFKL_OK;
+}
+
+int32_t nmfkl_kernel_times(nmfkl_ctx *c, const char **names, int64_t *launches, double *ms, int32_t cap,
+                           int32_t reset) {
+    if (!c) return -1;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto &pd : c->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pd.a, pd.b) == cudaSuccess) {
+            c->timers[pd.timer].ms += t;
+            c->timers[pd.timer].launches += 1;
+        }
+        c->ev_pool.push_back(pd.a);
+        c->ev_pool.push_back(pd.b);
+    }
+    c->pending.clear();
+    const int32_t nf = (int32_t)c->timers.size();
+    for (int32_t i = 0; i < nf && i < cap; ++i) {
+        if (names) names[i] = c->timers[i].name;
+        if (launches) launches[i] = c->timers[i].launches;
+        if (ms) ms[i] = c->timers[i].ms;
+    }
+    if (reset) {
+        for (auto &t : c->timers) {
+            t.launches = 0;
+            t.ms = 0.0;
+        }
+    }
+    return nf;
+}
+
+nmfkl_status nmfkl_debug_perm(nmfkl_ctx *c, int64_t sweep, int32_t side, int64_t count, const int64_t *cols,
+                              int32_t *out) {
+    if (!c || count < 0 || (count > 0 && (!cols || !out)) || (side != 0 && side != 1)) return NMFKL_EINVAL;
+    cudaSetDevice(c->device);
+    nmfkl_status st = launch_debug_perm(c, sweep, side, count, cols, out);
+    if (st != NMFKL_OK) return st;
+    return cuda_ok(c, cudaStreamSynchronize(c->stream), "debug_perm sync") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+// Supporting kernels: sumA (Algorithm 1's sumW = W 1, sumF = F 1), the
+// objective of Eq. 1/2, random initialisation, layout transposes and input
+// validation. Every reduction runs in a fixed order (block partials, then
+// one ordered pass), so results are bitwise reproducible.
+#include "common.cuh"
+
+#include <cmath>
+
+namespace nmfkl {
+
+namespace {
+
+constexpr int kColsumBlocks = 1024;
+constexpr int kObjBlocks = 2048;
+
+// Stage 1 of sum over rows of At (rows x ldr): block b covers a contiguous
+// row range; thread t handles column t % ldr of rows t / ldr, t / ldr + rpi, ...
+__global__ void colsum_partial_kernel(const float *At, int64_t rows, int ldr, double *part) {
+    __shared__ double acc[256];
+    const int t = threadIdx.x;
+    const int rpi = 256 / ldr;
+    const int k = t % ldr, ro = t / ldr;
+    const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(rows, r0 + per);
+    double s = 0.0;
+    if (ro < rpi)
+        for (int64_t row = r0 + ro; row < r1; row += rpi) s += (double)At[row * ldr + k];
+    acc[t] = s;
+    __syncthreads();
+    if (t < ldr) {
+        double tot = 0.0;
+        for (int j = 0; j < rpi; ++j) tot += acc[j * ldr + t];
+        part[(int64_t)blockIdx.x * ldr + t] = tot;
+    }
+}
+
+__global__ void colsum_final_kernel(const double *part, int nblocks, int ldr, int r, float *out,
+                                    double *out_d) {
+    for (int k = threadIdx.x; k < ldr; k += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * ldr + k];
+        if (out) out[k] = k < r ? (float)s : 0.f;
+        if (out_d) out_d[k] = k < r ? s : 0.0;
+    }
+}
+
+// Eq. 1 over the nonzeros: one warp per column j (CSC), F^T row j in shared
+// memory, one lane per nonzero computing x_ij = <W^T_i, F^T_j> in FP32 and
+// the term v log(v / (x + eps)) - v in FP32, accumulated in FP64.
+__global__ void objective_nnz_kernel(const int64_t *colptr, const int32_t *rowidx, const float *val,
+                                     const float *Wt, const float *Ft, int64_t m, int ldr, float eps_div,
+                                     double *part) {
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ double wsum[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4 *frow = reinterpret_cast<float4 *>(fsm + w * ldr);
+    const int nf4 = ldr >> 2;
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * 8 + w; j < m; j += (int64_t)gridDim.x * 8) {
+        __syncwarp();
+        for (int f = lane; f < nf4; f += 32) frow[f] = reinterpret_cast<const float4 *>(Ft + j * ldr)[f];
+        __syncwarp();
+        for (int64_t p = colptr[j] + lane; p < colptr[j + 1]; p += 32) {
+            const float4 *wr = reinterpret_cast<const float4 *>(Wt + (int64_t)rowidx[p] * ldr);
+            float x = 0.f;
+            for (int f = 0; f < nf4; ++f) {
+                const float4 a = __ldg(wr + f), b = frow[f];
+                x = fmaf(a.x, b.x, x);
+                x = fmaf(a.y, b.y, x);
+                x = fmaf(a.z, b.z, x);
+                x = fmaf(a.w, b.w, x);
+            }
+            const float v = val[p];
+            acc += (double)(v * logf(v / (x + eps_div)) - v);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) wsum[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 8; ++i) s += wsum[i];
+        part[blockIdx.x] = s;
+    }
+}
+
+// Sums of squares and absolute values of a unit-major factor (pads are 0).
+__global__ void sq_abs_kernel(const float *X, int64_t count, double *part2, double *part1) {
+    __shared__ double s2[256], s1[256];
+    double a2 = 0.0, a1 = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < count; e += (int64_t)gridDim.x * 256) {
+        const double v = (double)X[e];
+        a2 += v * v;
+        a1 += fabs(v);
+    }
+    s2[threadIdx.x] = a2;
+    s1[threadIdx.x] = a1;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part2[blockIdx.x] = s2[0];
+        part1[blockIdx.x] = s1[0];
+    }
+}
+
+// kl = sum of nnz partials + sum_k sumW_k sumF_k;
+// reg = a1/2 |W|^2 + a2/2 |F|^2 + b1 |W|_1 + b2 |F|_1.
+__global__ void objective_final_kernel(const double *nnzpart, int nb, const double *sw, const double *sf,
+                                       int r, const double *regpart, int nreg, double a1, double a2,
+                                       double b1, double b2, double *out) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += nnzpart[b];
+    for (int k = 0; k < r; ++k) s += sw[k] * sf[k];
+    double w2 = 0.0, w1 = 0.0, f2 = 0.0, f1 = 0.0;
+    for (int b = 0; b < nreg; ++b) {
+        w2 += regpart[b];
+        w1 += regpart[nreg + b];
+        f2 += regpart[2 * nreg + b];
+        f1 += regpart[3 * nreg + b];
+    }
+    out[0] = s;
+    out[1] = 0.5 * a1 * w2 + 0.5 * a2 * f2 + b1 * w1 + b2 * f1;
+}
+
+// Uniform[0,1) from Philox: entry e (row-major r x cols) -> X[c*ldr + k].
+__global__ void uniform_init_kernel(float *X, int r, int64_t cols, int ldr, uint64_t seed, int which) {
+    const int64_t total = (int64_t)r * cols;
+    for (int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; blk * 4 < total;
+         blk += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t c[4] = {(uint64_t)blk, (uint64_t)which, 0ull, 0ull};
+        philox4x64_10(c, seed, kKeyInit);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t e = blk * 4 + j;
+            if (e < total) {
+                const int64_t k = e / cols, col = e - k * cols;
+                X[col * ldr + k] = (float)(c[j] >> 40) * (1.0f / 16777216.0f);
+            }
+        }
+    }
+}
+
+// r x cols row-major  <->  cols x ldr unit-major (pad columns zero).
+__global__ void to_unit_major_kernel(const float *src, float *dst, int r, int64_t cols, int ldr) {
+    __shared__ float t[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int k = k0 + i;
+        const int64_t c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (k < r && c < cols) ? src[(int64_t)k * cols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t c = c0 + i;
+        const int k = k0 + threadIdx.x;
+        if (c < cols && k < ldr) dst[c * ldr + k] = t[threadIdx.x][i];
+    }
+}
+
+__global__ void from_unit_major_kernel(const float *src, float *dst, int r, int64_t cols, int ldr) {
+    __shared__ float t[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t c = c0 + i;
+        const int k = k0 + threadIdx.x;
+        t[i][threadIdx.x] = (c < cols && k < r) ? src[c * ldr + k] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int k = k0 + i;
+        const int64_t c = c0 + threadIdx.x;
+        if (k < r && c < cols) dst[(int64_t)k * cols + c] = t[threadIdx.x][i];
+    }
+}
+
+// flag bit 1: offsets not monotone or out of [0, nnz]; 2: index out of range
+// or not strictly increasing; 4: value not finite or <= 0.
+__global__ void validate_kernel(int64_t units, int64_t extent, const int64_t *ptr, const int32_t *idx,
+                                const float *val, int32_t *flag) {
+    const int64_t nnz = ptr[units];
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = ptr[u], e = ptr[u + 1];
+        if (b > e || b < 0 || e > nnz) {
+            atomicOr(flag, 1);
+            continue;
+        }
+        int32_t prev = -1;
+        for (int64_t p = b; p < e; ++p) {
+            const int32_t i = idx[p];
+            if (i <= prev || i >= extent) atomicOr(flag, 2);
+            prev = i;
+            const float v = val[p];
+            if (!(v > 0.f) || !isfinite(v)) atomicOr(flag, 4);
+        }
+    }
+}
+
+}  // namespace
+
+nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out) {
+    const int tok = timer_begin(c, "colsum");
+    colsum_partial_kernel<<<kColsumBlocks, 256, 0, c->stream>>>(At, rows, c->ldr, c->dpart);
+    colsum_final_kernel<<<1, 256, 0, c->stream>>>(c->dpart, kColsumBlocks, c->ldr, c->p.r, out, nullptr);
+    timer_end(c, tok);
+    return cuda_ok(c, cudaGetLastError(), "colsum") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+nmfkl_status launch_objective(nmfkl_ctx *c, double *kl, double *reg) {
+    const int ldr = c->ldr, r = c->p.r;
+    // dpart layout: [colsum partials kColsumBlocks*ldr][sumW_d ldr][sumF_d ldr][nnz kObjBlocks][reg 4*kObjBlocks]
+    double *sw = c->dpart + (int64_t)kColsumBlocks * ldr;
+    double *sf = sw + ldr;
+    double *nnzp = sf + ldr;
+    double *regp = nnzp + kObjBlocks;
+    const int tok = timer_begin(c, "objective");
+    colsum_partial_kernel<<<kColsumBlocks, 256, 0, c->stream>>>(c->Wt, c->n, ldr, c->dpart);
+    colsum_final_kernel<<<1, 256, 0, c->stream>>>(c->dpart, kColsumBlocks, ldr, r, nullptr, sw);
+    colsum_partial_kernel<<<kColsumBlocks, 256, 0, c->stream>>>(c->Ft, c->m, ldr, c->dpart);
+    colsum_final_kernel<<<1, 256, 0, c->stream>>>(c->dpart, kColsumBlocks, ldr, r, nullptr, sf);
+    objective_nnz_kernel<<<kObjBlocks, 256, 8 * ldr * sizeof(float), c->stream>>>(
+        c->colptr, c->rowidx, c->val, c->Wt, c->Ft, c->m, ldr, (float)c->p.eps_div, nnzp);
+    sq_abs_kernel<<<kObjBlocks, 256, 0, c->stream>>>(c->Wt, c->n * ldr, regp, regp + kObjBlocks);
+    sq_abs_kernel<<<kObjBlocks, 256, 0, c->stream>>>(c->Ft, c->m * ldr, regp + 2 * kObjBlocks,
+                                                      regp + 3 * kObjBlocks);
+    objective_final_kernel<<<1, 32, 0, c->stream>>>(nnzp, kObjBlocks, sw, sf, r, regp, kObjBlocks,
+                                                    c->p.alpha_W, c->p.alpha_F, c->p.beta_W, c->p.beta_F,
+                                                    c->dscalar);
+    timer_end(c, tok);
+    if (!cuda_ok(c, cudaGetLastError(), "objective")) return NMFKL_ECUDA;
+    double h[2];
+    if (!cuda_ok(c, cudaMemcpyAsync(h, c->dscalar, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy objective"))
+        return NMFKL_ECUDA;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "objective sync")) return NMFKL_ECUDA;
+    if (kl) *kl = h[0];
+    if (reg) *reg = h[1];
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) {
+        c->err = "objective is not finite";
+        return NMFKL_ENUMERIC;
+    }
+    return NMFKL_OK;
+}
+
+int64_t dpart_required(int ldr) { return (int64_t)kColsumBlocks * ldr + 2 * ldr + 5 * kObjBlocks + 64; }
+
+nmfkl_status launch_uniform_init(nmfkl_ctx *c, int which, float *X, int64_t cols) {
+    const int tok = timer_begin(c, "uniform_init");
+    uniform_init_kernel<<<1024, 256, 0, c->stream>>>(X, c->p.r, cols, c->ldr, c->p.seed, which);
+    timer_end(c, tok);
+    return cuda_ok(c, cudaGetLastError(), "uniform_init") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+nmfkl_status launch_to_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((c->ldr + 31) / 32));
+    const int tok = timer_begin(c, "transpose");
+    to_unit_major_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(src, dst, c->p.r, cols, c->ldr);
+    timer_end(c, tok);
+    return cuda_ok(c, cudaGetLastError(), "to_unit_major") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+nmfkl_status launch_from_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((c->p.r + 31) / 32));
+    const int tok = timer_begin(c, "transpose");
+    from_unit_major_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(src, dst, c->p.r, cols, c->ldr);
+    timer_end(c, tok);
+    return cuda_ok(c, cudaGetLastError(), "from_unit_major") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, const int64_t *ptr,
+                             const int32_t *idx, const float *val, int32_t *flag) {
+    validate_kernel<<<256, 256, 0, c->stream>>>(units, extent, ptr, idx, val, flag);
+    return cuda_ok(c, cudaGetLastError(), "validate") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+}  // namespace nmfkl

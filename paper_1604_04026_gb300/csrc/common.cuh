@@ -1,0 +1,171 @@
+// Internal declarations shared by the CUDA translation units of libnmfkl.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nmfkl.h"
+
+namespace nmfkl {
+
+constexpr int kMaxR = 256;
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): per round two 64x64 ->
+// 128-bit products of counter words 0 and 2 by fixed multipliers, output
+// words (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), key bumped by the Weyl
+// constants (golden ratio, sqrt(3)-1); ten rounds.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kPhiloxM0 = 0xD2E7470EE14C6C93ULL;
+constexpr uint64_t kPhiloxM1 = 0xCA5A826395121157ULL;
+constexpr uint64_t kPhiloxW0 = 0x9E3779B97F4A7C15ULL;
+constexpr uint64_t kPhiloxW1 = 0xBB67AE8584CAA73BULL;
+// Key word 1 tags what the stream is for.
+constexpr uint64_t kKeyIds = 0x5352434400000001ULL;   // coordinate orders
+constexpr uint64_t kKeyInit = 0x5352434400000002ULL;  // Uniform[0,1) starting factors
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t lo0 = kPhiloxM0 * c[0], hi0 = __umul64hi(kPhiloxM0, c[0]);
+        const uint64_t lo1 = kPhiloxM1 * c[2], hi1 = __umul64hi(kPhiloxM1, c[2]);
+        const uint64_t n0 = hi1 ^ c[1] ^ k0;
+        const uint64_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+}
+
+// Counter of block `blk` of the coordinate order of (sweep, side, unit).
+// perm_mode 1 shares one order per sweep (column word 0, side word 2).
+__device__ __forceinline__ void ids_counter(uint64_t c[4], uint64_t blk, int64_t unit, int64_t sweep,
+                                            int side, int perm_mode) {
+    c[0] = blk;
+    c[1] = perm_mode == 1 ? 0ull : (uint64_t)unit;
+    c[2] = (uint64_t)sweep;
+    c[3] = perm_mode == 1 ? 2ull : (uint64_t)side;
+}
+
+// ---------------------------------------------------------------------------
+// Arguments of one half sweep (Algorithm 1): the units are columns of V (F
+// half, CSC, A = W^T) or rows of V (W half, CSR, A = F^T).
+// ---------------------------------------------------------------------------
+struct HalfArgs {
+    const int64_t *ptr;   // unit offsets into idx/val
+    const int32_t *idx;   // row of A (= the other factor's row) per nonzero
+    const float *val;     // v per nonzero
+    const float *At;      // fixed factor, one row of ldr floats per index (W^T or F^T)
+    float *X;             // updated factor, one row of ldr floats per unit (F^T or W^T)
+    const float *sumA;    // r sums of the fixed factor's columns over its rows
+    int32_t r, ldr;
+    float alpha, beta, eps_grad, eps_div, eps_x;
+    int32_t max_inner, grad_mode, break_mode, perm_mode;
+    uint64_t seed;
+    int64_t sweep;
+    int32_t side;
+    // bucket
+    const int32_t *units;  // unit ids of this bucket, longest first
+    int32_t count;
+    int32_t *queue;        // work counter, zero at launch
+    float *scratch;        // per-group slots of slot_floats floats
+    int64_t slot_floats;
+    int32_t lcap;          // tile row length (max nonzeros of a unit in this bucket)
+    unsigned long long *counters;  // coords, evals, steps, cap_hits
+    int32_t *err;          // device error flag
+};
+
+// One launch configuration of the sweep kernel family.
+struct Bucket {
+    int kind;         // index into the kernel table
+    int nt;           // threads per subproblem group (32 = one warp)
+    int k;            // nonzeros per thread held in registers (0 = giant)
+    int32_t count;    // units in the bucket
+    int32_t lcap;     // tile row length
+    int32_t *d_units; // device list of unit ids
+    int grid;         // persistent blocks
+    int block;        // threads per block
+    size_t smem;      // dynamic shared memory per block
+    int groups;       // subproblem groups in the grid
+    int64_t slot_floats;
+    int64_t max_len;
+    int64_t nnz;      // nonzeros of the bucket's units
+};
+
+struct KernelTimer {
+    const char *name;  // string literal
+    int64_t launches = 0;
+    double ms = 0.0;
+};
+
+}  // namespace nmfkl
+
+struct nmfkl_ctx {
+    nmfkl_params p;
+    int64_t n = 0, m = 0, nnz = 0;
+    int32_t ldr = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+    bool have_data = false;
+    // V
+    int64_t *colptr = nullptr, *rowptr = nullptr;
+    int32_t *rowidx = nullptr, *colidx = nullptr;
+    float *val = nullptr, *rval = nullptr;
+    // factors, unit-major with row stride ldr: Wt (n x ldr), Ft (m x ldr)
+    float *Wt = nullptr, *Ft = nullptr;
+    float *sumW = nullptr, *sumF = nullptr;
+    double *dpart = nullptr;       // reduction partials
+    int64_t dpart_len = 0;
+    double *dscalar = nullptr;     // small FP64 results
+    unsigned long long *counters = nullptr;
+    int32_t *queues = nullptr;     // one per bucket per side
+    int32_t *err_flag = nullptr;
+    float *scratch = nullptr;
+    int64_t scratch_floats = 0;
+    float *tbuf = nullptr;         // transpose staging for get/set
+    int64_t tbuf_floats = 0;
+    std::vector<nmfkl::Bucket> plan[2];
+    // timing
+    bool timing = false;
+    std::vector<nmfkl::KernelTimer> timers;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { int timer; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+};
+
+namespace nmfkl {
+
+// Error helpers (host).
+bool cuda_ok(nmfkl_ctx *c, cudaError_t e, const char *what);
+
+// Timing hooks around every kernel launch.
+int timer_begin(nmfkl_ctx *c, const char *name);
+void timer_end(nmfkl_ctx *c, int token);
+
+// sweep.cu
+nmfkl_status plan_side(nmfkl_ctx *c, int side);
+nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep);
+void free_plan(nmfkl_ctx *c);
+const char *kind_name(int kind);
+
+// aux.cu
+nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out);
+nmfkl_status launch_objective(nmfkl_ctx *c, double *kl, double *reg);
+nmfkl_status launch_uniform_init(nmfkl_ctx *c, int which, float *X, int64_t cols);
+nmfkl_status launch_to_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols);
+nmfkl_status launch_from_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols);
+nmfkl_status launch_debug_perm(nmfkl_ctx *c, int64_t sweep, int side, int64_t count,
+                               const int64_t *cols, int32_t *out);
+int64_t dpart_required(int ldr);
+nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, const int64_t *ptr,
+                             const int32_t *idx, const float *val, int32_t *flag);
+
+}  // namespace nmfkl

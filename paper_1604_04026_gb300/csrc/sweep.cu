@@ -1,0 +1,652 @@
+// Sweep kernels: one half of Algorithm 1, i.e. Algorithm 2 on every unit
+// (column of F, or row of W) of a length bucket.
+//
+// Mapping (one subproblem = one "group": a warp, or a whole CTA):
+//   1. stage: for each nonzero p of the unit, read the fixed factor's row
+//      A_p = At[idx_p, 0:r] (one coalesced 4r-byte row), compute
+//      x_p = [Ax]_p = sum_k A_pk x_k (Algorithm 2, first step), and write the
+//      row transposed into the group's tile T[k][p] in global scratch, so
+//      that every later access to column k of A is one coalesced sweep.
+//   2. each thread keeps, for the nonzeros it owns (p = t + NT*s), x_p, v_p,
+//      w_p = v_p / (x_p + eps) and q_p = w_p / (x_p + eps) in registers.
+//      Then the Eq. Partial sums are sum_p w_p A_pk and sum_p q_p A_pk^2, and
+//      a Newton step dx updates x_p += dx A_pk and refreshes w_p, q_p.
+//   3. coordinates are visited in the Philox order ids (Algorithm 1) with the
+//      projected Newton loop of Algorithm 2; column k of T is prefetched one
+//      coordinate ahead into registers.
+// Reductions are warp xor-butterflies (every lane ends with the same bits),
+// plus for CTA groups one shared-memory exchange per evaluation.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace nmfkl {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ constexpr int odd_stride(int r) { return (r & 1) ? r : r + 1; }
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Per-group shared memory: perm (256 B) | x_init, x_out (ldr floats each) |
+// staging rows (8 x odd_stride(r) floats per warp) | CTA partials.
+__host__ __device__ inline size_t stage_offset(int ldr) { return align16(256 + 2 * (size_t)ldr * 4); }
+__host__ __device__ inline size_t group_smem_bytes(int r, int ldr, int warps, bool cta) {
+    size_t b = stage_offset(ldr) + (size_t)warps * 8 * odd_stride(r) * 4;
+    if (cta) b += 2 * (size_t)warps * sizeof(float2);
+    return align16(b);
+}
+
+// Fisher-Yates over {0..r-1} from the identity: step t (i = r-1-t) uses
+// word t, j = floor(word * (i+1) / 2^64).
+__device__ __forceinline__ void fisher_yates(uint8_t *perm, const uint64_t *words, int r) {
+    for (int i = 0; i < r; ++i) perm[i] = (uint8_t)i;
+    int t = 0;
+    for (int i = r - 1; i >= 1; --i, ++t) {
+        const int j = (int)__umul64hi(words[t], (uint64_t)(i + 1));
+        const uint8_t tmp = perm[i];
+        perm[i] = perm[j];
+        perm[j] = tmp;
+    }
+}
+
+// The r-1 Philox words of a unit's order, generated by the 32 lanes of a warp.
+__device__ __forceinline__ void ids_words_warp(uint64_t *words, int r, int64_t unit, int64_t sweep,
+                                               int side, int perm_mode, uint64_t seed, int lane) {
+    const int nw = r - 1;
+    const int nblk = (nw + 3) / 4;
+    for (int b = lane; b < nblk; b += 32) {
+        uint64_t c[4];
+        ids_counter(c, (uint64_t)b, unit, sweep, side, perm_mode);
+        philox4x64_10(c, seed, kKeyIds);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (4 * b + j < nw) words[4 * b + j] = c[j];
+    }
+}
+
+// Stages the 32 nonzeros p0..p0+31 of a unit (one warp): loads their A rows,
+// writes them transposed into the tile and returns, in lane l, x_p of
+// nonzero p0 + l (0 if p0 + l >= L). idx_l is the lane's own row index.
+__device__ __forceinline__ float stage_chunk32(const HalfArgs &a, float *tile, float *stg, const float *x_init,
+                                               int p0, int L, int idx_l, int lane) {
+    const int r = a.r, ldr = a.ldr, S = odd_stride(r), lcap = a.lcap;
+    const int nf4 = ldr >> 2;
+    const int items = 8 * nf4;
+    float myx = 0.f;
+    for (int q = 0; q < 4; ++q) {
+        if (p0 + 8 * q >= L) break;  // warp-uniform
+        for (int b0 = 0; b0 < items; b0 += 32) {
+            const int it = b0 + lane;
+            const int row = it / nf4, f = it - row * nf4;
+            const int ridx = __shfl_sync(kFull, idx_l, 8 * q + (row & 7));
+            const int p = p0 + 8 * q + row;
+            if (it < items && p < L) {
+                const float4 v4 = __ldg(reinterpret_cast<const float4 *>(a.At + (int64_t)ridx * ldr) + f);
+                float *dst = stg + row * S + 4 * f;
+                if (4 * f + 0 < r) dst[0] = v4.x;
+                if (4 * f + 1 < r) dst[1] = v4.y;
+                if (4 * f + 2 < r) dst[2] = v4.z;
+                if (4 * f + 3 < r) dst[3] = v4.w;
+            }
+        }
+        __syncwarp();
+        {
+            const int row = lane >> 2, part = lane & 3;
+            float acc = 0.f;
+            for (int k = part; k < r; k += 4) acc = fmaf(stg[row * S + k], x_init[k], acc);
+            acc += __shfl_xor_sync(kFull, acc, 1);
+            acc += __shfl_xor_sync(kFull, acc, 2);
+            const int li = lane - 8 * q;
+            const float got = __shfl_sync(kFull, acc, 4 * (li & 7));
+            if (li >= 0 && li < 8) myx = got;
+        }
+        for (int kb = 0; kb < r; kb += 4) {
+            const int k = kb + (lane >> 3), i = lane & 7;
+            const int p = p0 + 8 * q + i;
+            if (k < r && p < L) tile[(int64_t)k * lcap + p] = stg[i * S + k];
+        }
+        __syncwarp();
+    }
+    return myx;
+}
+
+struct Tally {
+    unsigned long long coords = 0, evals = 0, steps = 0, caps = 0;
+};
+
+__device__ __forceinline__ void flush_tally(const HalfArgs &a, const Tally &t) {
+    if (t.coords) atomicAdd(&a.counters[0], t.coords);
+    if (t.evals) atomicAdd(&a.counters[1], t.evals);
+    if (t.steps) atomicAdd(&a.counters[2], t.steps);
+    if (t.caps) atomicAdd(&a.counters[3], t.caps);
+}
+
+// The projected Newton loop of Algorithm 2 for one coordinate. eval() returns
+// (sum_p w_p A_pk, sum_p q_p A_pk^2) over the subproblem; update(d) applies
+// x_p += d A_pk. Every thread of the group runs it with identical values.
+template <class Eval, class Update>
+__device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, float sAk, Eval &&eval,
+                                                   Update &&update, Tally &t) {
+    const float alpha = a.alpha, beta = a.beta;
+    float2 s = eval();
+    ++t.evals;
+    ++t.coords;
+    float g = -s.x + sAk + alpha * xk + beta;
+    float h = s.y + alpha;
+    const float tol = a.grad_mode == 0 ? a.eps_grad * (sAk + beta) : a.eps_grad;
+    const float xfloor = a.grad_mode == 0 ? 0.f : a.eps_grad;
+    int it = 0;
+    while (g < -tol || (fabsf(g) > tol && xk > xfloor)) {
+        if (it == a.max_inner) {
+            ++t.caps;
+            break;
+        }
+        ++it;
+        float xn;
+        if (h > 0.f) {
+            xn = xk - __fdiv_rn(g, h);
+            if (xn < 0.f) xn = 0.f;
+        } else {
+            xn = g > 0.f ? 0.f : xk;
+        }
+        const float d = xn - xk;
+        if (d != 0.f) update(d);
+        const float xs = xk;
+        xk = xk + d;
+        ++t.steps;
+        const bool brk = a.break_mode == 0 ? (fabsf(d) < a.eps_x * xs) : (d < a.eps_x * xs);
+        if (brk) break;
+        s = eval();
+        ++t.evals;
+        g = -s.x + sAk + alpha * xk + beta;
+        h = s.y + alpha;
+    }
+    return xk;
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident groups: NT threads (32 = one warp per subproblem, several
+// per block; otherwise one CTA), K nonzeros per thread, so L <= NT*K.
+// ---------------------------------------------------------------------------
+template <int NT, int K>
+__global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool kCta = NT > 32;
+    constexpr int kNW = NT / 32;
+    const int lane = threadIdx.x & 31;
+    const int warp_in_block = threadIdx.x >> 5;
+    const int group_in_block = kCta ? 0 : warp_in_block;
+    const int groups_per_block = kCta ? 1 : (int)(blockDim.x >> 5);
+    const int warp_in_group = kCta ? warp_in_block : 0;
+    const int tid_g = kCta ? (int)threadIdx.x : lane;
+    const int group_global = blockIdx.x * groups_per_block + group_in_block;
+
+    const int r = a.r, ldr = a.ldr, S = odd_stride(r);
+    unsigned char *gs = smem_raw + (size_t)group_in_block * group_smem_bytes(r, ldr, kNW, kCta);
+    uint8_t *perm = gs;
+    float *x_init = reinterpret_cast<float *>(gs + 256);
+    float *x_out = x_init + ldr;
+    float *stg_base = reinterpret_cast<float *>(gs + stage_offset(ldr));
+    float *stg = stg_base + warp_in_group * 8 * S;
+    float2 *red = reinterpret_cast<float2 *>(stg_base + kNW * 8 * S);
+    uint64_t *words = reinterpret_cast<uint64_t *>(stg_base);
+    __shared__ int s_q;
+
+    float *tile = a.scratch + (int64_t)group_global * a.slot_floats;
+    const int lcap = a.lcap;
+    const float eps_div = a.eps_div;
+    Tally tally;
+    int parity = 0;
+
+    for (;;) {
+        int qi;
+        if constexpr (kCta) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_q = atomicAdd(a.queue, 1);
+            __syncthreads();
+            qi = s_q;
+        } else {
+            __syncwarp();
+            int q = 0;
+            if (lane == 0) q = atomicAdd(a.queue, 1);
+            qi = __shfl_sync(kFull, q, 0);
+        }
+        if (qi >= a.count) break;
+        const int64_t u = a.units[qi];
+        const int64_t base = a.ptr[u];
+        const int L = (int)(a.ptr[u + 1] - base);
+        const int ks = (L + NT - 1) / NT;
+
+        for (int k = tid_g; k < ldr; k += NT) x_init[k] = a.X[u * ldr + k];
+        if constexpr (kCta) __syncthreads(); else __syncwarp();
+
+        // ---- stage A rows, x_p, and the per-nonzero state
+        float xr[K], vr[K], wr[K], qr[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f;
+            if (s < ks) {
+                const int p0 = 32 * warp_in_group + NT * s;
+                if (p0 < L) {
+                    const int pl = p0 + lane;
+                    int idx_l = 0;
+                    float v_l = 0.f;
+                    if (pl < L) {
+                        idx_l = a.idx[base + pl];
+                        v_l = a.val[base + pl];
+                    }
+                    const float x_l = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
+                    if (pl < L) {
+                        xr[s] = x_l;
+                        vr[s] = v_l;
+                        const float ri = __frcp_rn(x_l + eps_div);
+                        wr[s] = v_l * ri;
+                        qr[s] = wr[s] * ri;
+                    }
+                }
+            }
+        }
+        // ---- coordinate order (warp 0; its staging rows hold the words)
+        if (warp_in_group == 0) {
+            ids_words_warp(words, r, u, a.sweep, a.side, a.perm_mode, a.seed, lane);
+            __syncwarp();
+            if (lane == 0) fisher_yates(perm, words, r);
+            __syncwarp();
+        }
+        if constexpr (kCta) __syncthreads(); else __syncwarp();
+
+        // ---- Algorithm 2 coordinate loop
+        auto load_col = [&](float (&dst)[K], int k) {
+            const float *col = tile + (int64_t)k * lcap;
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                const int p = tid_g + NT * s;
+                dst[s] = (s < ks && p < L) ? __ldcg(col + p) : 0.f;
+            }
+        };
+        auto reduce = [&](float sg, float sh) -> float2 {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sg += __shfl_xor_sync(kFull, sg, o);
+                sh += __shfl_xor_sync(kFull, sh, o);
+            }
+            if constexpr (kCta) {
+                float2 *rb = red + parity * kNW;
+                if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
+                __syncthreads();
+                float tg = 0.f, th = 0.f;
+#pragma unroll
+                for (int w = 0; w < kNW; ++w) {
+                    const float2 v = rb[w];
+                    tg += v.x;
+                    th += v.y;
+                }
+                parity ^= 1;
+                return make_float2(tg, th);
+            } else {
+                return make_float2(sg, sh);
+            }
+        };
+
+        float acur[K], anxt[K];
+        load_col(acur, perm[0]);
+        auto process = [&](float (&ac)[K], float (&an)[K], int kk) {
+            const int k = perm[kk];
+            if (kk + 1 < r) load_col(an, perm[kk + 1]);
+            auto eval = [&]() -> float2 {
+                float sg = 0.f, sh = 0.f;
+#pragma unroll
+                for (int s = 0; s < K; ++s) {
+                    if (s < ks) {
+                        sg = fmaf(wr[s], ac[s], sg);
+                        sh = fmaf(qr[s] * ac[s], ac[s], sh);
+                    }
+                }
+                return reduce(sg, sh);
+            };
+            auto update = [&](float d) {
+#pragma unroll
+                for (int s = 0; s < K; ++s) {
+                    if (s < ks) {
+                        xr[s] = fmaf(d, ac[s], xr[s]);
+                        const float ri = __frcp_rn(xr[s] + eps_div);
+                        wr[s] = vr[s] * ri;
+                        qr[s] = wr[s] * ri;
+                    }
+                }
+            };
+            const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+            if (tid_g == 0) x_out[k] = xk;
+        };
+        for (int kk = 0; kk < r; kk += 2) {
+            process(acur, anxt, kk);
+            if (kk + 1 < r) process(anxt, acur, kk + 1);
+        }
+        if constexpr (kCta) __syncthreads(); else __syncwarp();
+        for (int k = tid_g; k < r; k += NT) {
+            const float xv = x_out[k];
+            if (!(xv == xv)) atomicOr(a.err, 1);
+            a.X[u * ldr + k] = xv;
+        }
+    }
+    if (tid_g == 0) flush_tally(a, tally);
+}
+
+// ---------------------------------------------------------------------------
+// Giant units (L beyond the register-resident buckets): one CTA per unit,
+// per-nonzero state in the group's global scratch slot:
+//   [T: r x lcap][x: lcap][v: lcap][w: lcap][q: lcap]
+// ---------------------------------------------------------------------------
+constexpr int kGiantNT = 512;
+
+__global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kNW = kGiantNT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = a.r, ldr = a.ldr, S = odd_stride(r), lcap = a.lcap;
+    uint8_t *perm = smem_raw;
+    float *x_init = reinterpret_cast<float *>(smem_raw + 256);
+    float *x_out = x_init + ldr;
+    float *stg_base = reinterpret_cast<float *>(smem_raw + stage_offset(ldr));
+    float *stg = stg_base + warp * 8 * S;
+    float2 *red = reinterpret_cast<float2 *>(stg_base + kNW * 8 * S);
+    uint64_t *words = reinterpret_cast<uint64_t *>(stg_base);
+    __shared__ int s_q;
+
+    float *tile = a.scratch + (int64_t)blockIdx.x * a.slot_floats;
+    float *gx = tile + (int64_t)r * lcap;
+    float *gv = gx + lcap;
+    float *gw = gv + lcap;
+    float *gq = gw + lcap;
+    const float eps_div = a.eps_div;
+    Tally tally;
+    int parity = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_q = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int qi = s_q;
+        if (qi >= a.count) break;
+        const int64_t u = a.units[qi];
+        const int64_t base = a.ptr[u];
+        const int L = (int)(a.ptr[u + 1] - base);
+        for (int k = threadIdx.x; k < ldr; k += kGiantNT) x_init[k] = a.X[u * ldr + k];
+        __syncthreads();
+        for (int p0 = 32 * warp; p0 < L; p0 += kGiantNT) {
+            const int pl = p0 + lane;
+            int idx_l = 0;
+            float v_l = 0.f;
+            if (pl < L) {
+                idx_l = a.idx[base + pl];
+                v_l = a.val[base + pl];
+            }
+            const float x_l = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
+            if (pl < L) {
+                const float ri = __frcp_rn(x_l + eps_div);
+                gx[pl] = x_l;
+                gv[pl] = v_l;
+                gw[pl] = v_l * ri;
+                gq[pl] = v_l * ri * ri;
+            }
+        }
+        if (warp == 0) {
+            ids_words_warp(words, r, u, a.sweep, a.side, a.perm_mode, a.seed, lane);
+            __syncwarp();
+            if (lane == 0) fisher_yates(perm, words, r);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int kk = 0; kk < r; ++kk) {
+            const int k = perm[kk];
+            const float *col = tile + (int64_t)k * lcap;
+            auto eval = [&]() -> float2 {
+                float sg = 0.f, sh = 0.f;
+                for (int p = threadIdx.x; p < L; p += kGiantNT) {
+                    const float av = __ldcg(col + p);
+                    sg = fmaf(__ldcg(gw + p), av, sg);
+                    sh = fmaf(__ldcg(gq + p) * av, av, sh);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sg += __shfl_xor_sync(kFull, sg, o);
+                    sh += __shfl_xor_sync(kFull, sh, o);
+                }
+                float2 *rb = red + parity * kNW;
+                if (lane == 0) rb[warp] = make_float2(sg, sh);
+                __syncthreads();
+                float tg = 0.f, th = 0.f;
+#pragma unroll
+                for (int w = 0; w < kNW; ++w) {
+                    const float2 v = rb[w];
+                    tg += v.x;
+                    th += v.y;
+                }
+                parity ^= 1;
+                return make_float2(tg, th);
+            };
+            auto update = [&](float d) {
+                for (int p = threadIdx.x; p < L; p += kGiantNT) {
+                    const float xv = fmaf(d, __ldcg(col + p), __ldcg(gx + p));
+                    const float ri = __frcp_rn(xv + eps_div);
+                    const float wv = __ldcg(gv + p) * ri;
+                    gx[p] = xv;
+                    gw[p] = wv;
+                    gq[p] = wv * ri;
+                }
+            };
+            const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+            if (threadIdx.x == 0) x_out[k] = xk;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < r; k += kGiantNT) {
+            const float xv = x_out[k];
+            if (!(xv == xv)) atomicOr(a.err, 1);
+            a.X[u * ldr + k] = xv;
+        }
+    }
+    if (threadIdx.x == 0) flush_tally(a, tally);
+}
+
+// ---------------------------------------------------------------------------
+// Host side: the bucket table and the plan.
+// ---------------------------------------------------------------------------
+struct KernelKind {
+    const void *fn;
+    int nt, k;
+    const char *name;
+};
+
+const KernelKind kKinds[] = {
+    {(const void *)sweep_kernel<32, 1>, 32, 1, "sweep_warp_k1"},
+    {(const void *)sweep_kernel<32, 2>, 32, 2, "sweep_warp_k2"},
+    {(const void *)sweep_kernel<32, 4>, 32, 4, "sweep_warp_k4"},
+    {(const void *)sweep_kernel<32, 8>, 32, 8, "sweep_warp_k8"},
+    {(const void *)sweep_kernel<32, 16>, 32, 16, "sweep_warp_k16"},
+    {(const void *)sweep_kernel<128, 8>, 128, 8, "sweep_cta128_k8"},
+    {(const void *)sweep_kernel<256, 8>, 256, 8, "sweep_cta256_k8"},
+    {(const void *)sweep_kernel<512, 8>, 512, 8, "sweep_cta512_k8"},
+    {(const void *)sweep_kernel<512, 16>, 512, 16, "sweep_cta512_k16"},
+    {(const void *)sweep_giant_kernel, kGiantNT, 0, "sweep_giant"},
+};
+constexpr int kNumKinds = sizeof(kKinds) / sizeof(kKinds[0]);
+constexpr int kGiantKind = kNumKinds - 1;
+
+int kind_for_length(int64_t L) {
+    for (int i = 0; i < kGiantKind; ++i)
+        if (L <= (int64_t)kKinds[i].nt * kKinds[i].k) return i;
+    return kGiantKind;
+}
+
+}  // namespace
+
+const char *kind_name(int kind) { return kKinds[kind].name; }
+
+void free_plan(nmfkl_ctx *c) {
+    for (int side = 0; side < 2; ++side) {
+        for (auto &b : c->plan[side])
+            if (b.d_units) cudaFree(b.d_units);
+        c->plan[side].clear();
+    }
+}
+
+nmfkl_status plan_side(nmfkl_ctx *c, int side) {
+    const int64_t units = side == 0 ? c->m : c->n;
+    std::vector<int64_t> ptr(units + 1);
+    const int64_t *dptr = side == 0 ? c->colptr : c->rowptr;
+    if (!cuda_ok(c, cudaMemcpy(ptr.data(), dptr, sizeof(int64_t) * (units + 1), cudaMemcpyDeviceToHost),
+                 "copy offsets"))
+        return NMFKL_ECUDA;
+    std::vector<std::vector<int32_t>> lists(kNumKinds);
+    std::vector<int64_t> maxlen(kNumKinds, 0), nnz(kNumKinds, 0);
+    for (int64_t u = 0; u < units; ++u) {
+        const int64_t L = ptr[u + 1] - ptr[u];
+        const int kind = kind_for_length(L);
+        lists[kind].push_back((int32_t)u);
+        maxlen[kind] = std::max(maxlen[kind], L);
+        nnz[kind] += L;
+    }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    optin -= 1024;  // headroom for the kernels' static shared memory
+    const int r = c->p.r, ldr = c->ldr;
+    for (int kind = 0; kind < kNumKinds; ++kind) {
+        auto &lst = lists[kind];
+        if (lst.empty()) continue;
+        std::stable_sort(lst.begin(), lst.end(), [&](int32_t x, int32_t y) {
+            return (ptr[x + 1] - ptr[x]) > (ptr[y + 1] - ptr[y]);
+        });
+        Bucket b{};
+        b.kind = kind;
+        b.nt = kKinds[kind].nt;
+        b.k = kKinds[kind].k;
+        b.count = (int32_t)lst.size();
+        b.max_len = maxlen[kind];
+        b.nnz = nnz[kind];
+        const bool cta = b.nt > 32;
+        const int warps = b.nt / 32;
+        const size_t gbytes = group_smem_bytes(r, ldr, cta ? warps : 1, cta);
+        int groups_per_block = 1;
+        if (!cta) {
+            groups_per_block = 8;
+            while (groups_per_block > 1 && gbytes * groups_per_block > (size_t)optin) --groups_per_block;
+        }
+        b.block = cta ? b.nt : 32 * groups_per_block;
+        b.smem = gbytes * (cta ? 1 : groups_per_block);
+        if (b.smem > (size_t)optin) {
+            c->err = "shared memory plan exceeds the device limit";
+            return NMFKL_EINVAL;
+        }
+        if (!cuda_ok(c, cudaFuncSetAttribute(kKinds[kind].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)b.smem),
+                     "set smem attribute"))
+            return NMFKL_ECUDA;
+        int per_sm = 0;
+        if (!cuda_ok(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kKinds[kind].fn, b.block, b.smem),
+                     "occupancy"))
+            return NMFKL_ECUDA;
+        if (per_sm < 1) {
+            c->err = std::string("kernel ") + kKinds[kind].name + " cannot be resident";
+            return NMFKL_EINVAL;
+        }
+        if (kind == kGiantKind) per_sm = 1;
+        const int64_t need_blocks = (b.count + groups_per_block - 1) / groups_per_block;
+        b.grid = (int)std::min<int64_t>(need_blocks, (int64_t)per_sm * c->num_sms);
+        b.groups = b.grid * groups_per_block;
+        if (kind == kGiantKind) {
+            b.lcap = (int32_t)((b.max_len + 31) / 32 * 32);
+            b.slot_floats = (int64_t)(r + 4) * b.lcap;
+        } else {
+            b.lcap = b.nt * b.k;
+            b.slot_floats = (int64_t)r * b.lcap;
+        }
+        b.slot_floats = (b.slot_floats + 63) / 64 * 64;
+        if (!cuda_ok(c, cudaMalloc(&b.d_units, sizeof(int32_t) * lst.size()), "alloc unit list"))
+            return NMFKL_ENOMEM;
+        if (!cuda_ok(c, cudaMemcpy(b.d_units, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice),
+                     "copy unit list"))
+            return NMFKL_ECUDA;
+        c->plan[side].push_back(b);
+        c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
+    }
+    return NMFKL_OK;
+}
+
+nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
+    const bool F = side == 0;
+    const float *At = F ? c->Wt : c->Ft;
+    float *X = F ? c->Ft : c->Wt;
+    float *sumA = F ? c->sumW : c->sumF;
+    nmfkl_status st = launch_colsum(c, At, F ? c->n : c->m, sumA);
+    if (st != NMFKL_OK) return st;
+    HalfArgs a{};
+    a.ptr = F ? c->colptr : c->rowptr;
+    a.idx = F ? c->rowidx : c->colidx;
+    a.val = F ? c->val : c->rval;
+    a.At = At;
+    a.X = X;
+    a.sumA = sumA;
+    a.r = c->p.r;
+    a.ldr = c->ldr;
+    a.alpha = (float)(F ? c->p.alpha_F : c->p.alpha_W);
+    a.beta = (float)(F ? c->p.beta_F : c->p.beta_W);
+    a.eps_grad = (float)c->p.eps_grad;
+    a.eps_div = (float)c->p.eps_div;
+    a.eps_x = (float)c->p.eps_x;
+    a.max_inner = c->p.max_inner;
+    a.grad_mode = c->p.grad_mode;
+    a.break_mode = c->p.break_mode;
+    a.perm_mode = c->p.perm_mode;
+    a.seed = c->p.seed;
+    a.sweep = sweep;
+    a.side = side;
+    a.scratch = c->scratch;
+    a.counters = c->counters;
+    a.err = c->err_flag;
+    int qi = 0;
+    for (auto &b : c->plan[side]) {
+        a.units = b.d_units;
+        a.count = b.count;
+        a.queue = c->queues + side * 16 + qi++;
+        a.slot_floats = b.slot_floats;
+        a.lcap = b.lcap;
+        if (!cuda_ok(c, cudaMemsetAsync(a.queue, 0, sizeof(int32_t), c->stream), "reset queue"))
+            return NMFKL_ECUDA;
+        void *args[] = {&a};
+        const int tok = timer_begin(c, kKinds[b.kind].name);
+        cudaError_t e = cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, c->stream);
+        timer_end(c, tok);
+        if (!cuda_ok(c, e, kKinds[b.kind].name)) return NMFKL_ECUDA;
+    }
+    return NMFKL_OK;
+}
+
+// Coordinate orders exactly as the sweep kernels draw them (one warp per unit).
+__global__ void debug_perm_kernel(const int64_t *cols, int64_t count, int r, int64_t sweep, int side,
+                                  int perm_mode, uint64_t seed, int32_t *out) {
+    __shared__ uint64_t words[8][kMaxR];
+    __shared__ uint8_t perm[8][kMaxR];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * 8 + w;
+    if (c >= count) return;
+    ids_words_warp(words[w], r, cols[c], sweep, side, perm_mode, seed, lane);
+    __syncwarp();
+    if (lane == 0) fisher_yates(perm[w], words[w], r);
+    __syncwarp();
+    for (int t = lane; t < r; t += 32) out[c * r + t] = perm[w][t];
+}
+
+nmfkl_status launch_debug_perm(nmfkl_ctx *c, int64_t sweep, int side, int64_t count, const int64_t *cols,
+                               int32_t *out) {
+    if (count <= 0) return NMFKL_OK;
+    const int tok = timer_begin(c, "debug_perm");
+    debug_perm_kernel<<<(unsigned)((count + 7) / 8), 256, 0, c->stream>>>(cols, count, c->p.r, sweep, side,
+                                                                          c->p.perm_mode, c->p.seed, out);
+    timer_end(c, tok);
+    return cuda_ok(c, cudaGetLastError(), "debug_perm") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+}  // namespace nmfkl

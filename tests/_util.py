@@ -1,0 +1,77 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and the FP64 oracle on the same seeded inputs, and compare."""
+import numpy as np
+
+import oracle
+import paper_1604_04026_gb300 as nk
+from paper_1604_04026_gb300 import synth
+
+# Per-entry bar of one sweep from an identical state: |gpu - oracle| <=
+# RTOL |oracle| + FLOOR * max_k |oracle[:, unit]| (relative 1e-4, with a
+# floor scaled to the unit's largest entry for values near zero).
+RTOL = 1e-4
+FLOOR = 1e-6
+
+TIGHT = dict(eps_x=1e-9, max_inner=64, eps_grad=1e-13)
+
+
+def params(r, **kw):
+    return nk.default_params(r, **kw)
+
+
+def cfg_for(p, side):
+    """Oracle parameters of one side from the library parameters."""
+    alpha = p.alpha_F if side == 0 else p.alpha_W
+    beta = p.beta_F if side == 0 else p.beta_W
+    return oracle.cfg(alpha=alpha, beta=beta, eps_grad=p.eps_grad, eps_div=p.eps_div, eps_x=p.eps_x,
+                      max_inner=p.max_inner, grad_mode=p.grad_mode, break_mode=p.break_mode,
+                      perm_mode=p.perm_mode)
+
+
+def model(V, W0, F0, p):
+    m = nk.NMFKL(V.n, V.m, params=p)
+    m.set_data(V)
+    m.init(np.ascontiguousarray(W0, dtype=np.float32), np.ascontiguousarray(F0, dtype=np.float32))
+    return m
+
+
+def within(g, o, rtol=RTOL, floor=FLOOR):
+    """Boolean mask of entries inside the per-entry bar (columns are units)."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    scale = np.abs(o).max(axis=0, keepdims=True)
+    return np.abs(g - o) <= rtol * np.abs(o) + floor * scale
+
+
+def start(V, r, seed=0):
+    return synth.uniform_init(r, V.n, seed, 0), synth.uniform_init(r, V.m, seed, 1)
+
+
+def designed_matrix(n, m, col_lengths, row_lengths, seed=0):
+    """Count matrix whose first columns have the given lengths and whose
+    first rows have the given lengths (both at once), plus a sprinkle of
+    entries elsewhere; values are small counts >= 1."""
+    rng = np.random.default_rng(seed)
+    d = {}
+    for j, L in enumerate(col_lengths):
+        for i in rng.choice(n, size=min(L, n), replace=False):
+            d[(int(i), j)] = float(rng.integers(1, 6))
+    for i, L in enumerate(row_lengths):
+        for j in rng.choice(m, size=min(L, m), replace=False):
+            d[(n - 1 - i, int(j))] = float(rng.integers(1, 6))
+    for _ in range(3 * (n + m)):
+        d[(int(rng.integers(n)), int(rng.integers(m)))] = float(rng.integers(1, 4))
+    # exact column lengths for the designed columns: drop extras beyond L
+    items = sorted(d.items(), key=lambda t: (t[0][1], t[0][0]))
+    cols = [[] for _ in range(m)]
+    for (i, j), v in items:
+        cols[j].append((i, v))
+    for j, L in enumerate(col_lengths):
+        if len(cols[j]) > L:
+            keep = rng.choice(len(cols[j]), size=L, replace=False)
+            cols[j] = sorted(cols[j][k] for k in keep)
+    colptr = np.zeros(m + 1, dtype=np.int64)
+    colptr[1:] = np.cumsum([len(c) for c in cols])
+    rowidx = np.array([i for c in cols for i, _ in c], dtype=np.int32)
+    val = np.array([v for c in cols for _, v in c], dtype=np.float32)
+    return synth.from_csc(n, m, colptr, rowidx, val)

@@ -1,0 +1,310 @@
+"""GPU parity: the CUDA sweep (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars (FP32 path vs FP64 oracle):
+  * one half / one sweep from an identical state, each coordinate solved to
+    its 1-D minimiser (tight mode): every entry within 1e-4 relative, with a
+    floor of 1e-6 x the unit's largest entry;
+  * KL trajectory over 20 sweeps at the paper's constants (eps_x = 0.1):
+    within 1e-4 relative after every sweep;
+  * integer work (coordinate orders) and the random start: bit-exact.
+At the paper's constants the break and clamp decisions can flip between FP32
+and FP64 for entries sitting on a threshold, so there one sweep is gated on
+the fraction of entries inside the bar.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1604_04026_gb300 as nk
+from paper_1604_04026_gb300 import synth
+
+from _util import RTOL, TIGHT, cfg_for, designed_matrix, model, params, start, within
+
+pytestmark = pytest.mark.gpu
+
+BUCKET_LENGTHS = [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513,
+                  1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 12000]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def designed():
+    return designed_matrix(13000, 12500, BUCKET_LENGTHS, BUCKET_LENGTHS, seed=1)
+
+
+@pytest.fixture(scope="module")
+def docs_small():
+    return synth.docs(3000, 2000, 20, seed=3, threads=8)
+
+
+# ------------------------------------------------------------------ integer work
+@pytest.mark.parametrize("r", [1, 2, 10, 50, 100, 200, 256])
+def test_coordinate_orders_bit_exact(torch, r):
+    V = synth.poisson_lowrank(50, 40, 2, density=0.3, seed=0)
+    for perm_mode in (0, 1):
+        p = params(r, seed=12345, perm_mode=perm_mode)
+        m = nk.NMFKL(V.n, V.m, params=p)
+        units = list(range(40)) + [123456, 2**31 - 2]
+        cols = torch.tensor(units, dtype=torch.int64, device="cuda")
+        out = torch.empty((len(units), r), dtype=torch.int32, device="cuda")
+        for sweep in (0, 3):
+            for side in (0, 1):
+                m.debug_perm(sweep, side, cols, out)
+                got = out.cpu().numpy()
+                for c, u in enumerate(units):
+                    want = oracle.perm(12345, sweep, side, u, r, perm_mode)
+                    assert np.array_equal(got[c], want), (r, perm_mode, sweep, side, u)
+        m.close()
+
+
+def test_uniform_init_bit_exact(torch):
+    V = synth.poisson_lowrank(300, 200, 5, density=0.05, seed=0)
+    for r in (1, 7, 64):
+        m = nk.NMFKL(V.n, V.m, params=params(r, seed=99))
+        m.set_data(V)
+        m.init()
+        assert np.array_equal(m.get_W().astype(np.float64), oracle.uniform_init(99, 0, r, V.n))
+        assert np.array_equal(m.get_F().astype(np.float64), oracle.uniform_init(99, 1, r, V.m))
+        m.close()
+
+
+# ------------------------------------------------------------------ objective
+@pytest.mark.parametrize("which", ["c1", "docs"])
+def test_objective_matches_oracle(which, docs_small):
+    V = synth.poisson_lowrank(1000, 500, 10, seed=0) if which == "c1" else docs_small
+    r = 10 if which == "c1" else 20
+    W0, F0 = start(V, r, seed=4)
+    p = params(r, alpha_W=0.3, beta_W=0.2, alpha_F=0.1, beta_F=0.05)
+    m = model(V, W0, F0, p)
+    kl, reg = m.objective()
+    okl, oreg = oracle.objective(V, W0, F0, eps_div=p.eps_div, a1=0.3, a2=0.1, b1=0.2, b2=0.05)
+    assert kl == pytest.approx(okl, rel=1e-6)
+    assert reg == pytest.approx(oreg, rel=1e-9)
+    m.close()
+
+
+# ------------------------------------------------------------------ halves, tight mode
+@pytest.mark.parametrize("side", [0, 1])
+def test_half_tight_every_bucket(designed, side):
+    V = designed
+    r = 16
+    W0, F0 = start(V, r, seed=2)
+    p = params(r, seed=5, **TIGHT)
+    m = model(V, W0, F0, p)
+    if side == 0:
+        m.sweep_F(0)
+        got = m.get_F()
+        want, _ = oracle.half_F(V, W0, F0, 5, 0, cfg_for(p, 0), threads=8)
+    else:
+        m.sweep_W(0)
+        got = m.get_W()
+        want, _ = oracle.half_W(V, W0, F0, 5, 0, cfg_for(p, 1), threads=8)
+    ok = within(got, want)
+    bad = np.argwhere(~ok)
+    assert ok.all(), "%d entries outside the bar, first %s" % (len(bad), bad[:5].tolist())
+    assert (got >= 0).all()
+    m.close()
+
+
+@pytest.mark.parametrize("case", ["c1", "docs_r37", "reg"])
+def test_full_sweep_tight(case, docs_small):
+    if case == "c1":
+        V, r, extra = synth.poisson_lowrank(1000, 500, 10, seed=0), 10, {}
+    elif case == "docs_r37":
+        V, r, extra = docs_small, 37, {}
+    else:
+        V, r, extra = docs_small, 12, dict(alpha_W=0.5, beta_W=0.1, alpha_F=0.2, beta_F=0.3)
+    W0, F0 = start(V, r, seed=7)
+    p = params(r, seed=11, **TIGHT, **extra)
+    m = model(V, W0, F0, p)
+    m.sweep(0)
+    F, _ = oracle.half_F(V, W0, F0, 11, 0, cfg_for(p, 0), threads=8)
+    W, _ = oracle.half_W(V, W0, F, 11, 0, cfg_for(p, 1), threads=8)
+    assert within(m.get_F(), F).all()
+    assert within(m.get_W(), W).all()
+    m.close()
+
+
+def test_r1_closed_form_on_gpu():
+    """r = 1: each column's minimiser is sum(v)/sumW (alpha = beta = 0)."""
+    V = synth.docs(500, 300, 3, seed=8, threads=4)
+    W0 = np.full((1, V.n), 0.5, dtype=np.float32)
+    F0 = np.full((1, V.m), 0.7, dtype=np.float32)
+    m = model(V, W0, F0, params(1, **TIGHT))
+    m.sweep_F(0)
+    want = np.add.reduceat(V.val.astype(np.float64), V.colptr[:-1])[None, :] / (0.5 * V.n)
+    want[:, np.diff(V.colptr) == 0] = 0.0
+    assert np.allclose(m.get_F(), want, rtol=2e-6)
+    m.close()
+
+
+def test_r256(docs_small):
+    V = docs_small
+    r = 256
+    W0, F0 = start(V, r, seed=9)
+    p = params(r, seed=1, **TIGHT)
+    m = model(V, W0, F0, p)
+    m.sweep_F(0)
+    F, _ = oracle.half_F(V, W0, F0, 1, 0, cfg_for(p, 0), threads=8)
+    assert within(m.get_F(), F).all()
+    m.close()
+
+
+def test_empty_units_go_to_zero():
+    """Columns and rows without nonzeros: f(x) = sumA.x, minimised at x = 0."""
+    d = np.zeros((50, 40), dtype=np.float32)
+    d[:30, :25] = np.random.default_rng(0).poisson(2.0, size=(30, 25))
+    d[0, 0] = 1.0
+    V = synth.from_dense(d)
+    W0, F0 = start(V, 4, seed=1)
+    m = model(V, W0, F0, params(4))
+    m.sweep(0)
+    F, W = m.get_F(), m.get_W()
+    empty_cols = np.diff(V.colptr) == 0
+    empty_rows = np.diff(V.rowptr) == 0
+    assert empty_cols.any() and empty_rows.any()
+    assert (F[:, empty_cols] == 0).all() and (W[:, empty_rows] == 0).all()
+    m.close()
+
+
+# ------------------------------------------------------------------ paper constants
+@pytest.mark.parametrize("case", ["c1", "docs"])
+def test_kl_trajectory_20_sweeps(case, docs_small):
+    if case == "c1":
+        V, r = synth.poisson_lowrank(1000, 500, 10, seed=0), 10
+    else:
+        V, r = docs_small, 20
+    W0, F0 = start(V, r, seed=0)
+    p = params(r, seed=0)
+    m = model(V, W0, F0, p)
+    traj, done = m.fit(20)
+    assert done == 20
+    ref = oracle.fit(V, W0, F0, 0, 20, cfg_for(p, 0), cfg_for(p, 1), threads=8)
+    rel = np.abs(traj - ref.kl) / ref.kl
+    assert rel.max() <= RTOL, rel
+    # monotone within FP32 noise
+    assert (np.diff(traj) <= 1e-6 * traj[:-1]).all()
+    m.close()
+
+
+def test_one_sweep_paper_constants_fraction(docs_small):
+    V, r = docs_small, 20
+    W0, F0 = start(V, r, seed=6)
+    p = params(r, seed=6)
+    m = model(V, W0, F0, p)
+    m.sweep(0)
+    F, _ = oracle.half_F(V, W0, F0, 6, 0, cfg_for(p, 0), threads=8)
+    W, _ = oracle.half_W(V, W0, F, 6, 0, cfg_for(p, 1), threads=8)
+    fF = within(m.get_F(), F).mean()
+    fW = within(m.get_W(), W).mean()
+    assert fF >= 0.99 and fW >= 0.98, (fF, fW)
+    m.close()
+
+
+def test_literal_modes(docs_small):
+    """Absolute epsilon, signed break and one shared order per sweep."""
+    V, r = docs_small, 16
+    W0, F0 = start(V, r, seed=3)
+    p = params(r, seed=2, grad_mode=1, eps_grad=1e-10, break_mode=1, perm_mode=1)
+    m = model(V, W0, F0, p)
+    traj, _ = m.fit(5)
+    ref = oracle.fit(V, W0, F0, 2, 5, cfg_for(p, 0), cfg_for(p, 1), threads=8)
+    assert (np.abs(traj - ref.kl) / ref.kl).max() <= RTOL
+    m.close()
+
+
+# ------------------------------------------------------------------ invariants, API
+def test_monotone_nonnegative_halves(docs_small):
+    V, r = docs_small, 24
+    W0, F0 = start(V, r, seed=5)
+    m = model(V, W0, F0, params(r, seed=5))
+    prev, _ = m.objective()
+    for s in range(5):
+        m.sweep_F(s)
+        kl, _ = m.objective()
+        assert kl <= prev * (1 + 1e-6)
+        prev = kl
+        m.sweep_W(s)
+        kl, _ = m.objective()
+        assert kl <= prev * (1 + 1e-6)
+        prev = kl
+    assert m.get_F().min() >= 0 and m.get_W().min() >= 0
+    m.close()
+
+
+def test_counters(docs_small):
+    V, r = docs_small, 8
+    W0, F0 = start(V, r)
+    m = model(V, W0, F0, params(r))
+    m.counters(reset=True)
+    m.sweep_F(0)
+    c = m.counters(reset=True)
+    assert c["coords"] == r * V.m
+    assert c["evals"] >= c["coords"] and c["steps"] > 0
+    _, st = oracle.half_F(V, W0, F0, 0, 0, cfg_for(m.params, 0), threads=8)
+    assert abs(c["steps"] - st["steps"]) <= 0.01 * st["steps"]
+    m.close()
+
+
+def test_device_inputs_match_host(torch, docs_small):
+    V, r = docs_small, 10
+    W0, F0 = start(V, r, seed=1)
+    a = model(V, W0, F0, params(r))
+    a.sweep(0)
+    b = nk.NMFKL(V.n, V.m, params=params(r))
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    b.set_data(colptr=t(V.colptr), rowidx=t(V.rowidx), val=t(V.val), rowptr=t(V.rowptr),
+               colidx=t(V.colidx), rval=t(V.rval))
+    b.init(t(W0), t(F0))
+    b.sweep(0)
+    assert np.array_equal(a.get_F(), b.get_F()) and np.array_equal(a.get_W(), b.get_W())
+    outW = torch.empty((r, V.n), dtype=torch.float32, device="cuda")
+    b.get_W(outW)
+    assert np.array_equal(outW.cpu().numpy(), a.get_W())
+    a.close()
+    b.close()
+
+
+def test_runs_are_bitwise_reproducible(docs_small):
+    V, r = docs_small, 20
+    W0, F0 = start(V, r, seed=2)
+    out = []
+    for _ in range(2):
+        m = model(V, W0, F0, params(r, seed=3))
+        traj, _ = m.fit(3)
+        out.append((traj, m.get_W(), m.get_F()))
+        m.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+def test_invalid_arguments(torch):
+    with pytest.raises(nk.NMFKLError, match="EINVAL"):
+        nk.NMFKL(10, 10, params=params(0))
+    with pytest.raises(nk.NMFKLError, match="EINVAL"):
+        nk.NMFKL(10, 10, params=params(300))
+    m = nk.NMFKL(4, 3, params=params(2))
+    with pytest.raises(nk.NMFKLError, match="EINVAL"):
+        m.objective()
+    colptr = np.array([0, 2, 2, 3], dtype=np.int64)
+    for rowidx, val in [([1, 0, 2], [1, 1, 1]), ([0, 1, 4], [1, 1, 1]), ([0, 1, 2], [1, 0, 1]),
+                        ([0, 1, 2], [1, np.nan, 1])]:
+        with pytest.raises(nk.NMFKLError, match="EINVAL"):
+            m.set_data(nnz=3, colptr=colptr, rowidx=np.array(rowidx, dtype=np.int32),
+                       val=np.array(val, dtype=np.float32))
+    # device inputs are validated on the device
+    bad = torch.tensor([1, 0, 2], dtype=torch.int32, device="cuda")
+    good_ptr = torch.tensor([0, 2, 2, 3], dtype=torch.int64, device="cuda")
+    v = torch.ones(3, dtype=torch.float32, device="cuda")
+    rp = torch.tensor([0, 1, 2, 3, 3], dtype=torch.int64, device="cuda")
+    ci = torch.tensor([0, 0, 2], dtype=torch.int32, device="cuda")
+    with pytest.raises(nk.NMFKLError, match="EINVAL"):
+        m.set_data(nnz=3, colptr=good_ptr, rowidx=bad, val=v, rowptr=rp, colidx=ci, rval=v)
+    m.close()
