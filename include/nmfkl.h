@@ -63,7 +63,7 @@ typedef struct {
     double beta_F;        /* b2: L1 weight on F */
     double eps_grad;      /* gradient tolerance of Algorithm 2's while test; default 1e-6 */
     double eps_div;       /* added to [Ax]_i in every division and log (Algorithm 2's
-                             log([Ax]_i + eps)); default 1e-10 */
+                             log([Ax]_i + eps)); default 1e-6 */
     double eps_x;         /* relative step that ends a coordinate's Newton loop;
                              default 0.1 (Section 3) */
     int32_t max_inner;    /* cap on Newton steps per coordinate; default 16 */

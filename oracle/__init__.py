@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
-def cfg(alpha=0.0, beta=0.0, eps_grad=1e-6, eps_div=1e-10, eps_x=0.1, max_inner=16,
+def cfg(alpha=0.0, beta=0.0, eps_grad=1e-6, eps_div=1e-6, eps_x=0.1, max_inner=16,
         grad_mode=0, break_mode=0, perm_mode=0) -> Cfg:
     """Defaults: eps_x = 0.1 (Section 3); the rest are this project's readings."""
     return Cfg(alpha, beta, eps_grad, eps_div, eps_x, max_inner, grad_mode, break_mode, perm_mode)
@@ -194,7 +194,7 @@ def half_W(V, W, F, seed, sweep, c: Cfg | None = None, threads: int = 1):
     return W, st.as_dict()
 
 
-def objective(V, W, F, eps_div=1e-10, a1=0.0, a2=0.0, b1=0.0, b2=0.0):
+def objective(V, W, F, eps_div=1e-6, a1=0.0, a2=0.0, b1=0.0, b2=0.0):
     """(Eq. 1 value, Eq. 2 regularizer) at W (r x n), F (r x m)."""
     W = _f64(W)
     F = _f64(F)
@@ -205,7 +205,7 @@ def objective(V, W, F, eps_div=1e-10, a1=0.0, a2=0.0, b1=0.0, b2=0.0):
     return kl.value, reg.value
 
 
-def column_objective(V, W, F, j, alpha=0.0, beta=0.0, eps_div=1e-10) -> float:
+def column_objective(V, W, F, j, alpha=0.0, beta=0.0, eps_div=1e-6) -> float:
     W = _f64(W)
     F = _f64(F)
     sumW = rowsum(W)

@@ -131,7 +131,7 @@ void nmfkl_default_params(nmfkl_params *p, int32_t r) {
     std::memset(p, 0, sizeof(*p));
     p->r = r;
     p->eps_grad = 1e-6;
-    p->eps_div = 1e-10;
+    p->eps_div = 1e-6;
     p->eps_x = 0.1;
     p->max_inner = 16;
     p->seed = 0;

@@ -69,13 +69,20 @@ __device__ __forceinline__ void ids_words_warp(uint64_t *words, int r, int64_t u
 
 // Stages the 32 nonzeros p0..p0+31 of a unit (one warp): loads their A rows,
 // writes them transposed into the tile and returns, in lane l, x_p of
-// nonzero p0 + l (0 if p0 + l >= L). idx_l is the lane's own row index.
-__device__ __forceinline__ float stage_chunk32(const HalfArgs &a, float *tile, float *stg, const float *x_init,
-                                               int p0, int L, int idx_l, int lane) {
+// nonzero p0 + l (0 if p0 + l >= L) and the number of coordinates with
+// A_pk > 0 and x_k > 0 (the positive terms of x_p). idx_l is the lane's own
+// row index.
+struct Staged {
+    float x;
+    int terms;
+};
+__device__ __forceinline__ Staged stage_chunk32(const HalfArgs &a, float *tile, float *stg, const float *x_init,
+                                                int p0, int L, int idx_l, int lane) {
     const int r = a.r, ldr = a.ldr, S = odd_stride(r), lcap = a.lcap;
     const int nf4 = ldr >> 2;
     const int items = 8 * nf4;
     float myx = 0.f;
+    int myc = 0;
     for (int q = 0; q < 4; ++q) {
         if (p0 + 8 * q >= L) break;  // warp-uniform
         for (int b0 = 0; b0 < items; b0 += 32) {
@@ -96,12 +103,23 @@ __device__ __forceinline__ float stage_chunk32(const HalfArgs &a, float *tile, f
         {
             const int row = lane >> 2, part = lane & 3;
             float acc = 0.f;
-            for (int k = part; k < r; k += 4) acc = fmaf(stg[row * S + k], x_init[k], acc);
+            int cnt = 0;
+            for (int k = part; k < r; k += 4) {
+                const float av = stg[row * S + k], xv = x_init[k];
+                acc = fmaf(av, xv, acc);
+                cnt += (av > 0.f && xv > 0.f);
+            }
             acc += __shfl_xor_sync(kFull, acc, 1);
             acc += __shfl_xor_sync(kFull, acc, 2);
+            cnt += __shfl_xor_sync(kFull, cnt, 1);
+            cnt += __shfl_xor_sync(kFull, cnt, 2);
             const int li = lane - 8 * q;
             const float got = __shfl_sync(kFull, acc, 4 * (li & 7));
-            if (li >= 0 && li < 8) myx = got;
+            const int gotc = __shfl_sync(kFull, cnt, 4 * (li & 7));
+            if (li >= 0 && li < 8) {
+                myx = got;
+                myc = gotc;
+            }
         }
         for (int kb = 0; kb < r; kb += 4) {
             const int k = kb + (lane >> 3), i = lane & 7;
@@ -110,7 +128,18 @@ __device__ __forceinline__ float stage_chunk32(const HalfArgs &a, float *tile, f
         }
         __syncwarp();
     }
-    return myx;
+    return Staged{myx, myc};
+}
+
+// x_p after a step of coordinate k: x_p + d A_pk, where `dc` (+1, -1 or 0)
+// records whether x_k just became positive or just became zero. x_p is a
+// sum of nonnegative terms A_pk x_k; `terms` counts the positive ones. When
+// it reaches 0 the exact value is 0, and any FP32 residual left by the
+// incremental updates is dropped; otherwise the value is kept >= 0.
+__device__ __forceinline__ float step_x(float x, float av, float d, int dc, int &terms) {
+    x = fmaf(d, av, x);
+    if (av > 0.f) terms += dc;
+    return terms == 0 ? 0.f : fmaxf(x, 0.f);
 }
 
 struct Tally {
@@ -125,8 +154,9 @@ __device__ __forceinline__ void flush_tally(const HalfArgs &a, const Tally &t) {
 }
 
 // The projected Newton loop of Algorithm 2 for one coordinate. eval() returns
-// (sum_p w_p A_pk, sum_p q_p A_pk^2) over the subproblem; update(d) applies
-// x_p += d A_pk. Every thread of the group runs it with identical values.
+// (sum_p w_p A_pk, sum_p q_p A_pk^2) over the subproblem; update(d, dc)
+// applies x_p += d A_pk (dc: x_k became positive (+1) or zero (-1)). Every
+// thread of the group runs it with identical values.
 template <class Eval, class Update>
 __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, float sAk, Eval &&eval,
                                                    Update &&update, Tally &t) {
@@ -153,9 +183,11 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
             xn = g > 0.f ? 0.f : xk;
         }
         const float d = xn - xk;
-        if (d != 0.f) update(d);
+        const float xnew = xk + d;
+        const int dc = (xk == 0.f && xnew > 0.f) ? 1 : ((xk > 0.f && xnew == 0.f) ? -1 : 0);
+        if (d != 0.f) update(d, dc);
         const float xs = xk;
-        xk = xk + d;
+        xk = xnew;
         ++t.steps;
         const bool brk = a.break_mode == 0 ? (fabsf(d) < a.eps_x * xs) : (d < a.eps_x * xs);
         if (brk) break;
@@ -225,9 +257,10 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
 
         // ---- stage A rows, x_p, and the per-nonzero state
         float xr[K], vr[K], wr[K], qr[K];
+        int cr[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
-            xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f;
+            xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
             if (s < ks) {
                 const int p0 = 32 * warp_in_group + NT * s;
                 if (p0 < L) {
@@ -238,9 +271,11 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
                         idx_l = a.idx[base + pl];
                         v_l = a.val[base + pl];
                     }
-                    const float x_l = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
+                    const Staged st = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
                     if (pl < L) {
+                        const float x_l = st.terms == 0 ? 0.f : st.x;
                         xr[s] = x_l;
+                        cr[s] = st.terms;
                         vr[s] = v_l;
                         const float ri = __frcp_rn(x_l + eps_div);
                         wr[s] = v_l * ri;
@@ -307,11 +342,11 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
                 }
                 return reduce(sg, sh);
             };
-            auto update = [&](float d) {
+            auto update = [&](float d, int dc) {
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
                     if (s < ks) {
-                        xr[s] = fmaf(d, ac[s], xr[s]);
+                        xr[s] = step_x(xr[s], ac[s], d, dc, cr[s]);
                         const float ri = __frcp_rn(xr[s] + eps_div);
                         wr[s] = vr[s] * ri;
                         qr[s] = wr[s] * ri;
@@ -338,7 +373,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
 // ---------------------------------------------------------------------------
 // Giant units (L beyond the register-resident buckets): one CTA per unit,
 // per-nonzero state in the group's global scratch slot:
-//   [T: r x lcap][x: lcap][v: lcap][w: lcap][q: lcap]
+//   [T: r x lcap][x: lcap][v: lcap][w: lcap][q: lcap][terms: lcap]
 // ---------------------------------------------------------------------------
 constexpr int kGiantNT = 512;
 
@@ -361,6 +396,7 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
     float *gv = gx + lcap;
     float *gw = gv + lcap;
     float *gq = gw + lcap;
+    int *gc = reinterpret_cast<int *>(gq + lcap);
     const float eps_div = a.eps_div;
     Tally tally;
     int parity = 0;
@@ -384,9 +420,11 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
                 idx_l = a.idx[base + pl];
                 v_l = a.val[base + pl];
             }
-            const float x_l = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
+            const Staged st = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
             if (pl < L) {
+                const float x_l = st.terms == 0 ? 0.f : st.x;
                 const float ri = __frcp_rn(x_l + eps_div);
+                gc[pl] = st.terms;
                 gx[pl] = x_l;
                 gv[pl] = v_l;
                 gw[pl] = v_l * ri;
@@ -428,9 +466,11 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
                 parity ^= 1;
                 return make_float2(tg, th);
             };
-            auto update = [&](float d) {
+            auto update = [&](float d, int dc) {
                 for (int p = threadIdx.x; p < L; p += kGiantNT) {
-                    const float xv = fmaf(d, __ldcg(col + p), __ldcg(gx + p));
+                    int terms = __ldcg(gc + p);
+                    const float xv = step_x(__ldcg(gx + p), __ldcg(col + p), d, dc, terms);
+                    gc[p] = terms;
                     const float ri = __frcp_rn(xv + eps_div);
                     const float wv = __ldcg(gv + p) * ri;
                     gx[p] = xv;
@@ -558,7 +598,7 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
         b.groups = b.grid * groups_per_block;
         if (kind == kGiantKind) {
             b.lcap = (int32_t)((b.max_len + 31) / 32 * 32);
-            b.slot_floats = (int64_t)(r + 4) * b.lcap;
+            b.slot_floats = (int64_t)(r + 5) * b.lcap;
         } else {
             b.lcap = b.nt * b.k;
             b.slot_floats = (int64_t)r * b.lcap;

@@ -12,7 +12,11 @@ from paper_1604_04026_gb300 import synth
 RTOL = 1e-4
 FLOOR = 1e-6
 
-TIGHT = dict(eps_x=1e-9, max_inner=64, eps_grad=1e-13)
+# Each coordinate solved to its 1-D minimiser: the Newton loop runs until its
+# step is below 1e-7 relative (reachable in FP32; quadratic convergence puts
+# the FP64 result ~1e-14 from the minimiser), the gradient test is far below
+# FP32 noise, and the cap is high enough for the log-barrier regrowth from 0.
+TIGHT = dict(eps_x=1e-7, max_inner=64, eps_grad=1e-9)
 
 
 def params(r, **kw):
@@ -33,6 +37,35 @@ def model(V, W0, F0, p):
     m.set_data(V)
     m.init(np.ascontiguousarray(W0, dtype=np.float32), np.ascontiguousarray(F0, dtype=np.float32))
     return m
+
+
+def unit_objectives(V, W, F, side, alpha=0.0, beta=0.0, eps_div=1e-6):
+    """Subproblem objective (Eq. kl) of every unit at (W, F), in FP64 numpy:
+    side 0: per column j of F, side 1: per row i of W."""
+    W = np.asarray(W, dtype=np.float64)
+    F = np.asarray(F, dtype=np.float64)
+    if side == 0:
+        units, ptr, idx, val = V.m, V.colptr, V.rowidx, V.val
+        other_of = np.repeat(np.arange(units), np.diff(ptr))
+        x = np.einsum("kp,kp->p", W[:, idx], F[:, other_of])
+        X, S = F, W.sum(axis=1)
+    else:
+        units, ptr, idx, val = V.n, V.rowptr, V.colidx, V.rval
+        other_of = np.repeat(np.arange(units), np.diff(ptr))
+        x = np.einsum("kp,kp->p", F[:, idx], W[:, other_of])
+        X, S = W, F.sum(axis=1)
+    v = val.astype(np.float64)
+    terms = v * np.log(v / (x + eps_div)) - v
+    data = np.zeros(units)
+    np.add.at(data, other_of, terms)
+    return data + S @ X + 0.5 * alpha * (X * X).sum(axis=0) + beta * np.abs(X).sum(axis=0)
+
+
+def objective_rel(V, Wg, Fg, Wo, Fo, side, alpha=0.0, beta=0.0, eps_div=1e-6):
+    """max over units of |D_u(gpu) - D_u(oracle)| / max(|D_u(oracle)|, 1)."""
+    dg = unit_objectives(V, Wg, Fg, side, alpha, beta, eps_div)
+    do = unit_objectives(V, Wo, Fo, side, alpha, beta, eps_div)
+    return float((np.abs(dg - do) / np.maximum(np.abs(do), 1.0)).max())
 
 
 def within(g, o, rtol=RTOL, floor=FLOOR):

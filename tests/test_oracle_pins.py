@@ -198,7 +198,7 @@ def _solve_full(v_all, A_all, alpha, beta, sweeps=200):
     r = A_all.shape[1]
     x = np.full(r, 0.5)
     S = A_all.sum(axis=0)
-    c = oracle.tight_cfg(alpha=alpha, beta=beta)
+    c = oracle.tight_cfg(alpha=alpha, beta=beta, eps_div=0.0)
     for s in range(sweeps):
         x, _ = oracle.alg2(v_all[nz], A_all[nz], S, x, oracle.perm(1, s, 0, 0, r), c)
     return x
@@ -359,7 +359,7 @@ def test_kkt_at_convergence():
     r = 3
     W = synth.uniform_init(r, V.n, 2, 0) + 0.1
     F = synth.uniform_init(r, V.m, 2, 1) + 0.1
-    c = oracle.tight_cfg()
+    c = oracle.tight_cfg(eps_div=0.0)
     res = oracle.fit(V, W, F, seed=0, sweeps=400, cF=c, cW=c, trace=False)
     # F was just solved with W fixed: its KKT holds to the solver tolerance
     W2, F2 = res.W, res.F
@@ -378,7 +378,8 @@ def test_foldin_recovers_exact_fit():
     Ft = rng.uniform(0.2, 2.0, size=(r, m))
     V = synth.from_dense(W.T @ Ft)  # every entry stored, FP32-rounded values
     F0 = np.full((r, m), 0.5)
-    F, done = oracle.foldin(V, W, F0, seed=3, rel_tol=1e-14, max_sweeps=3000, c=oracle.tight_cfg())
+    F, done = oracle.foldin(V, W, F0, seed=3, rel_tol=1e-14, max_sweeps=3000,
+                            c=oracle.tight_cfg(eps_div=0.0))
     assert np.allclose(F, Ft, rtol=1e-4, atol=1e-5)
     assert done.max() <= 3000
 
