@@ -52,7 +52,8 @@ class Cfg(ctypes.Structure):
                 ("eps_grad", ctypes.c_double), ("eps_div", ctypes.c_double),
                 ("eps_x", ctypes.c_double), ("max_inner", ctypes.c_int32),
                 ("grad_mode", ctypes.c_int32), ("break_mode", ctypes.c_int32),
-                ("perm_mode", ctypes.c_int32)]
+                ("perm_mode", ctypes.c_int32), ("perturb", ctypes.c_double),
+                ("perturb_seed", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):
@@ -64,9 +65,11 @@ class Stats(ctypes.Structure):
 
 
 def cfg(alpha=0.0, beta=0.0, eps_grad=1e-6, eps_div=1e-6, eps_x=0.1, max_inner=16,
-        grad_mode=0, break_mode=0, perm_mode=0) -> Cfg:
-    """Defaults: eps_x = 0.1 (Section 3); the rest are this project's readings."""
-    return Cfg(alpha, beta, eps_grad, eps_div, eps_x, max_inner, grad_mode, break_mode, perm_mode)
+        grad_mode=0, break_mode=0, perm_mode=0, perturb=0.0, perturb_seed=0) -> Cfg:
+    """Defaults: eps_x = 0.1 (Section 3); the rest are this project's readings.
+    perturb > 0 turns on the Monte Carlo arithmetic probe (see srcd_oracle.c)."""
+    return Cfg(alpha, beta, eps_grad, eps_div, eps_x, max_inner, grad_mode, break_mode, perm_mode,
+               perturb, perturb_seed)
 
 
 def tight_cfg(**kw) -> Cfg:

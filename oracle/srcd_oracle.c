@@ -129,6 +129,14 @@ typedef struct {
     int32_t grad_mode;     /* 0: eps_grad*(sumA_k+beta) and x_k>0; 1: absolute eps both places */
     int32_t break_mode;    /* 0: |dx| < eps_x*xs; 1: dx < eps_x*xs */
     int32_t perm_mode;     /* 0: ids per (sweep, side, column); 1: one ids per sweep */
+    double perturb;        /* 0 (default): exact FP64. > 0: Monte Carlo arithmetic
+                              probe (Parker 1997): [Ax]_p is multiplied by
+                              (1 + perturb*xi), xi ~ U(-1, 1), after every update,
+                              and by (1 + sqrt(r)*perturb*xi) after the initial sum,
+                              to measure how far rounding of x at that relative level
+                              moves each result (tests use perturb = 2^-24, FP32's
+                              unit roundoff). */
+    uint64_t perturb_seed; /* stream of the probe; each unit mixes in its index */
 } oracle_cfg;
 
 typedef struct {
@@ -153,15 +161,26 @@ void oracle_derivatives(int64_t L, const double *v, const double *A, int32_t r, 
     *h = s2 + c->alpha;
 }
 
+/* Uniform(-1, 1) from a splitmix64 stream (probe only). */
+static double probe_xi(uint64_t *state) {
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
 /* Updates x (length r) in place. ids is the coordinate order. Ax is scratch
  * of length L. */
 void oracle_alg2(int64_t L, const double *v, const double *A, const double *sumA, double *x,
                  int32_t r, const int32_t *ids, const oracle_cfg *c, double *Ax, oracle_stats *st) {
+    uint64_t probe = c->perturb_seed;
     /* Compute Ax on the nonzeros (Algorithm 2, first step). */
     for (int64_t p = 0; p < L; ++p) {
         double s = 0.0;
         for (int32_t k = 0; k < r; ++k) s += A[p * r + k] * x[k];
         Ax[p] = s;
+        if (c->perturb > 0.0) Ax[p] *= 1.0 + sqrt((double)r) * c->perturb * probe_xi(&probe);
     }
     for (int32_t kk = 0; kk < r; ++kk) {
         int32_t k = ids[kk];
@@ -179,6 +198,8 @@ void oracle_alg2(int64_t L, const double *v, const double *A, const double *sumA
             else xn = g > 0.0 ? 0.0 : x[k];
             double dx = xn - x[k];
             for (int64_t p = 0; p < L; ++p) Ax[p] += dx * A[p * r + k];
+            if (c->perturb > 0.0)
+                for (int64_t p = 0; p < L; ++p) Ax[p] *= 1.0 + c->perturb * probe_xi(&probe);
             double xs = x[k];
             x[k] = x[k] + dx;
             if (st) st->steps++;
@@ -235,7 +256,9 @@ static void *half_worker(void *arg) {
         }
         for (int32_t k = 0; k < r; ++k) x[k] = J->X[(int64_t)k * J->nx + u];
         oracle_perm(J->seed, J->sweep, J->side, u, J->cfg->perm_mode, r, ids);
-        oracle_alg2(L, v, A, J->sumA, x, r, ids, J->cfg, Ax, &J->st);
+        oracle_cfg cu = *J->cfg;
+        cu.perturb_seed = J->cfg->perturb_seed ^ ((uint64_t)u * 0xD1B54A32D192ED03ULL);
+        oracle_alg2(L, v, A, J->sumA, x, r, ids, &cu, Ax, &J->st);
         for (int32_t k = 0; k < r; ++k) J->X[(int64_t)k * J->nx + u] = x[k];
     }
     free(v); free(A); free(Ax); free(x); free(ids);

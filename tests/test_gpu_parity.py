@@ -2,13 +2,15 @@
 the same seeded inputs.
 
 Bars (FP32 path vs FP64 oracle), each half from an identical state:
-  * tight mode (every coordinate solved to its 1-D minimiser): the per-unit
-    subproblem objective within 1e-6 relative; every entry of units longer
-    than 256 within 1e-4 relative (floor 1e-6 x the unit's largest entry);
-    at least 99.5% of all entries within that bar;
-  * the paper's constants (eps_x = 0.1): at least 99% of entries within the
-    bar, per-unit objective within 1e-5, and the KL trajectory over 20 sweeps
-    within 1e-4 relative after every sweep;
+  * tight mode (every coordinate solved to its 1-D minimiser): every entry
+    within 1e-4 relative + 1e-6 x the unit's largest entry + 4 x its FP32
+    sensitivity (Monte Carlo arithmetic on the oracle, see fp32_sensitivity);
+    the per-unit subproblem objective within 2e-6 of the magnitude of its
+    terms (plus 4 x its probe spread);
+  * the paper's constants (eps_x = 0.1): at least 99.5% of entries within the
+    same bar (a break or clamp decision can flip between FP32 and FP64 for
+    an entry on its threshold), per-unit objective within 1e-5, and the KL
+    trajectory over 20 sweeps within 1e-4 relative after every sweep;
   * integer work (coordinate orders) and the random start: bit-exact.
 """
 import numpy as np
@@ -18,7 +20,8 @@ import oracle
 import paper_1604_04026_gb300 as nk
 from paper_1604_04026_gb300 import synth
 
-from _util import RTOL, TIGHT, cfg_for, designed_matrix, model, objective_rel, params, start, within
+from _util import (PROBE_FACTOR, RTOL, TIGHT, cfg_for, designed_matrix, fp32_sensitivity, model,
+                   objective_scale, params, start, unit_objectives, within)
 
 pytestmark = pytest.mark.gpu
 
@@ -92,13 +95,16 @@ def test_objective_matches_oracle(which, docs_small):
 # ------------------------------------------------------------------ halves, tight mode
 # From an identical state: the F half from (W0, F0) on both sides; the W half
 # from (W0, F1) on both sides, F1 being the oracle's F half (an oracle value).
-# Gates: the per-unit subproblem objective (Eq. kl, convex in the unit's
-# vector, so well conditioned) within OBJ_REL; every entry of units longer
-# than 256 inside the per-entry bar; and at least ENTRY_FRACTION of all
-# entries inside it. The few entries outside sit in short units whose
-# coordinates are nearly tied; their objective still agrees.
-ENTRY_FRACTION = 0.995
-OBJ_REL = 1e-6
+# Per-entry bar: |gpu - oracle| <= 1e-4 |oracle| + 1e-6 max_k |oracle[:, unit]|
+# + PROBE_FACTOR x the entry's FP32 sensitivity (fp32_sensitivity: how far the
+# FP64 oracle's entry moves when its model values x_p are perturbed at FP32's
+# unit roundoff; x runs in FP32 on the GPU). Most entries have a sensitivity
+# far below 1e-4 of their value, so the relative bar binds; a coordinate that
+# carries a small share of its x_p, or whose coordinates are nearly tied, gets
+# the slack its conditioning demands. The per-unit objective (Eq. kl) must
+# agree within OBJ_REL of the magnitude of its terms plus the same multiple
+# of the spread the probe runs show.
+OBJ_REL = 2e-6
 
 
 def _halves(V, W0, F0, p, threads=8):
@@ -117,17 +123,26 @@ def _halves(V, W0, F0, p, threads=8):
     return Fg, Fo, Wg, Wo, F1
 
 
-def _check_halves(V, W0, Fg, Fo, Wg, Wo, F1, p, fraction=ENTRY_FRACTION, obj_rel=OBJ_REL):
-    for side, got, want, lens in ((0, Fg, Fo, np.diff(V.colptr)), (1, Wg, Wo, np.diff(V.rowptr))):
-        ok = within(got, want)
-        assert ok.mean() >= fraction, (side, ok.mean())
-        long_units = lens > 256
-        assert ok[:, long_units].all(), (side, np.argwhere(~ok[:, long_units])[:5])
+def _check_halves(V, W0, F0, Fg, Fo, Wg, Wo, F1, p, fraction=1.0, obj_rel=OBJ_REL):
+    for side, got, want, start_F in ((0, Fg, Fo, F0), (1, Wg, Wo, F1)):
+        dev, probes = fp32_sensitivity(V, W0, start_F, side, p, want)
+        ok = within(got, want, slack=PROBE_FACTOR * dev)
+        bad = np.argwhere(~ok)
+        assert ok.mean() >= fraction, (side, ok.mean(), [(int(k), int(u), float(got[k, u]), float(want[k, u]))
+                                                           for k, u in bad[:4]])
         assert (got >= 0).all()
-    alpha_F, beta_F, alpha_W, beta_W = p.alpha_F, p.beta_F, p.alpha_W, p.beta_W
-    rF = objective_rel(V, W0, Fg, W0, Fo, 0, alpha_F, beta_F, p.eps_div)
-    rW = objective_rel(V, Wg, F1, Wo, F1, 1, alpha_W, beta_W, p.eps_div)
-    assert rF <= obj_rel and rW <= obj_rel, (rF, rW)
+        # per-unit objective of Eq. kl, with the same probe-measured slack
+        alpha, beta = (p.alpha_F, p.beta_F) if side == 0 else (p.alpha_W, p.beta_W)
+        if side == 0:
+            ev = lambda X: unit_objectives(V, W0, X, 0, alpha, beta, p.eps_div)
+            scale = objective_scale(V, W0, want, 0, alpha, beta, p.eps_div)
+        else:
+            ev = lambda X: unit_objectives(V, X, F1, 1, alpha, beta, p.eps_div)
+            scale = objective_scale(V, want, F1, 1, alpha, beta, p.eps_div)
+        d_ref = ev(want)
+        d_dev = np.max([np.abs(ev(x) - d_ref) for x in probes], axis=0)
+        err = np.abs(ev(got) - d_ref)
+        assert (err <= obj_rel * scale + PROBE_FACTOR * d_dev).all(), (side, float((err / scale).max()))
 
 
 def test_halves_tight_every_bucket(designed):
@@ -136,7 +151,7 @@ def test_halves_tight_every_bucket(designed):
     r = 16
     W0, F0 = start(V, r, seed=2)
     p = params(r, seed=5, **TIGHT)
-    _check_halves(V, W0, *_halves(V, W0, F0, p), p)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
 
 
 @pytest.mark.parametrize("case", ["c1", "docs_r37", "reg"])
@@ -149,7 +164,7 @@ def test_halves_tight(case, docs_small):
         V, r, extra = docs_small, 12, dict(alpha_W=0.5, beta_W=0.1, alpha_F=0.2, beta_F=0.3)
     W0, F0 = start(V, r, seed=7)
     p = params(r, seed=11, **TIGHT, **extra)
-    _check_halves(V, W0, *_halves(V, W0, F0, p), p)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
 
 
 def test_r1_closed_form_on_gpu():
@@ -159,9 +174,12 @@ def test_r1_closed_form_on_gpu():
     F0 = np.full((1, V.m), 0.7, dtype=np.float32)
     m = model(V, W0, F0, params(1, **TIGHT))
     m.sweep_F(0)
-    want = np.add.reduceat(V.val.astype(np.float64), V.colptr[:-1])[None, :] / (0.5 * V.n)
+    # all A entries are 0.5: g = -sum(v) 0.5 / (0.5 f + eps) + 0.5 n = 0
+    # gives f* = sum(v) / (0.5 n) - eps / 0.5
+    eps = m.params.eps_div
+    want = np.add.reduceat(V.val.astype(np.float64), V.colptr[:-1])[None, :] / (0.5 * V.n) - eps / 0.5
     want[:, np.diff(V.colptr) == 0] = 0.0
-    assert np.allclose(m.get_F(), want, rtol=2e-6)
+    assert np.allclose(m.get_F(), want, rtol=2e-6, atol=1e-7)
     m.close()
 
 
@@ -170,7 +188,7 @@ def test_r256(docs_small):
     r = 256
     W0, F0 = start(V, r, seed=9)
     p = params(r, seed=1, **TIGHT)
-    _check_halves(V, W0, *_halves(V, W0, F0, p), p)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
 
 
 def test_empty_units_go_to_zero():
@@ -218,7 +236,7 @@ def test_halves_paper_constants(case, docs_small):
     V, r = (synth.poisson_lowrank(1000, 500, 10, seed=0), 10) if case == "c1" else (docs_small, 20)
     W0, F0 = start(V, r, seed=6)
     p = params(r, seed=6)
-    _check_halves(V, W0, *_halves(V, W0, F0, p), p, fraction=0.99, obj_rel=1e-5)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, fraction=0.995, obj_rel=1e-5)
 
 
 def test_literal_modes(docs_small):

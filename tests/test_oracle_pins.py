@@ -396,3 +396,22 @@ def test_foldin_stops_on_relative_change():
         Fj, _ = oracle.foldin(V, W, F, seed=0, rel_tol=0.0, max_sweeps=1)
         assert Fj.min() >= 0
         assert d0 >= 0
+
+
+def test_rounding_probe_off_by_default_and_deterministic():
+    """The Monte Carlo arithmetic probe (used only to size FP32 bars) leaves
+    the FP64 path untouched at perturb = 0, is reproducible per seed and
+    independent of the thread count, and moves results by a small amount."""
+    V = synth.docs(400, 300, 5, seed=2, threads=2)
+    r = 8
+    W0 = synth.uniform_init(r, V.n, 0, 0)
+    F0 = synth.uniform_init(r, V.m, 0, 1)
+    base, _ = oracle.half_F(V, W0, F0, 1, 0, oracle.cfg())
+    same, _ = oracle.half_F(V, W0, F0, 1, 0, oracle.cfg(perturb=0.0, perturb_seed=7))
+    assert np.array_equal(base, same)
+    a, _ = oracle.half_F(V, W0, F0, 1, 0, oracle.cfg(perturb=2**-24, perturb_seed=7), threads=1)
+    b, _ = oracle.half_F(V, W0, F0, 1, 0, oracle.cfg(perturb=2**-24, perturb_seed=7), threads=4)
+    c, _ = oracle.half_F(V, W0, F0, 1, 0, oracle.cfg(perturb=2**-24, perturb_seed=8))
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c) and not np.array_equal(a, base)
+    assert np.abs(a - base).max() < 1e-2 * np.abs(base).max()
