@@ -140,7 +140,8 @@ nmfkl_status nmfkl_sweep_W(nmfkl_ctx *ctx, int64_t sweep);
 nmfkl_status nmfkl_objective(nmfkl_ctx *ctx, double *kl, double *reg);
 
 /* Algorithm 1 from the current state: sweeps s = sweep0, sweep0+1, ... (F
- * half then W half) until |D_s - D_{s-1}| <= rel_tol * D_{s-1} or
+ * half then W half, objective fused as in nmfkl_step) until
+ * |D_s - D_{s-1}| <= rel_tol * D_{s-1} or
  * max_sweeps. kl_trace (host, max_sweeps doubles, may be NULL) receives
  * Eq. 1 after each sweep; *sweeps_done (may be NULL) the count. Returns
  * ENOTCONV when max_sweeps ran out first and rel_tol > 0. */
@@ -149,6 +150,8 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *ctx, int64_t sweep0, int32_t max_sweeps, doubl
 
 /* One full pass of the hot path: nmfkl_sweep_F(sweep), nmfkl_sweep_W(sweep),
  * then Eq. 1 into *kl (may be NULL) for Algorithm 1's convergence test.
+ * The objective is fused into the W half: each row's data term is summed
+ * from its final model values, then sumW . sumF is added (FP64).
  * Synchronizes (the objective is read back). */
 nmfkl_status nmfkl_step(nmfkl_ctx *ctx, int64_t sweep, double *kl);
 

@@ -177,7 +177,8 @@ nmfkl_status nmfkl_create(const nmfkl_params *p, int64_t n, int64_t m, int32_t d
               dev_alloc(c, &c->sumW, c->ldr, "sumW") && dev_alloc(c, &c->sumF, c->ldr, "sumF") &&
               dev_alloc(c, &c->dpart, c->dpart_len, "partials") && dev_alloc(c, &c->dscalar, 8, "scalars") &&
               dev_alloc(c, &c->counters, 8, "counters") && dev_alloc(c, &c->queues, 64, "queues") &&
-              dev_alloc(c, &c->err_flag, 1, "error flag");
+              dev_alloc(c, &c->err_flag, 1, "error flag") && dev_alloc(c, &c->dsum[0], c->ldr, "sumW64") &&
+              dev_alloc(c, &c->dsum[1], c->ldr, "sumF64") && dev_alloc(c, &c->unit_obj, n, "row objective");
     if (!ok) {
         nmfkl_destroy(c);
         return NMFKL_ENOMEM;
@@ -201,6 +202,7 @@ void nmfkl_destroy(nmfkl_ctx *c) {
     cudaFree(c->Wt); cudaFree(c->Ft); cudaFree(c->sumW); cudaFree(c->sumF); cudaFree(c->dpart);
     cudaFree(c->dscalar); cudaFree(c->counters); cudaFree(c->queues); cudaFree(c->err_flag);
     cudaFree(c->tbuf);
+    cudaFree(c->dsum[0]); cudaFree(c->dsum[1]); cudaFree(c->unit_obj);
     for (auto &pd : c->pending) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -381,7 +383,7 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *c, int64_t sweep0, int32_t max_sweeps, double 
         st = run_half(c, 0, sweep0 + s);
         if (st == NMFKL_OK) st = run_half(c, 1, sweep0 + s);
         double kl = 0.0;
-        if (st == NMFKL_OK) st = launch_objective(c, &kl, nullptr);
+        if (st == NMFKL_OK) st = launch_fused_objective(c, &kl);
         if (st != NMFKL_OK) {
             if (sweeps_done) *sweeps_done = s;
             return st;
@@ -413,7 +415,7 @@ nmfkl_status nmfkl_step(nmfkl_ctx *c, int64_t sweep, double *kl) {
     cudaSetDevice(c->device);
     nmfkl_status st = run_half(c, 0, sweep);
     if (st == NMFKL_OK) st = run_half(c, 1, sweep);
-    if (st == NMFKL_OK) st = launch_objective(c, kl, nullptr);
+    if (st == NMFKL_OK) st = launch_fused_objective(c, kl);
     return st;
 }
 

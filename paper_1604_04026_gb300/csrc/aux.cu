@@ -207,10 +207,10 @@ __global__ void validate_kernel(int64_t units, int64_t extent, const int64_t *pt
 
 }  // namespace
 
-nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out) {
+nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out, double *out_d) {
     const int tok = timer_begin(c, "colsum");
     colsum_partial_kernel<<<kColsumBlocks, 256, 0, c->stream>>>(At, rows, c->ldr, c->dpart);
-    colsum_final_kernel<<<1, 256, 0, c->stream>>>(c->dpart, kColsumBlocks, c->ldr, c->p.r, out, nullptr);
+    colsum_final_kernel<<<1, 256, 0, c->stream>>>(c->dpart, kColsumBlocks, c->ldr, c->p.r, out, out_d);
     timer_end(c, tok);
     return cuda_ok(c, cudaGetLastError(), "colsum") ? NMFKL_OK : NMFKL_ECUDA;
 }
@@ -244,6 +244,46 @@ nmfkl_status launch_objective(nmfkl_ctx *c, double *kl, double *reg) {
     if (kl) *kl = h[0];
     if (reg) *reg = h[1];
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) {
+        c->err = "objective is not finite";
+        return NMFKL_ENUMERIC;
+    }
+    return NMFKL_OK;
+}
+
+// Eq. 1 after a W half: the per-row data terms the W half left in unit_obj
+// (summed in row order) plus the closed form sum_k sumW_k sumF_k.
+__global__ void fused_objective_kernel(const double *unit_obj, int64_t n, const double *sw, const double *sf,
+                                       int r, double *out) {
+    __shared__ double acc[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += unit_obj[i];
+    acc[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) acc[threadIdx.x] += acc[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double t = acc[0];
+        for (int k = 0; k < r; ++k) t += sw[k] * sf[k];
+        out[0] = t;
+    }
+}
+
+nmfkl_status launch_fused_objective(nmfkl_ctx *c, double *kl) {
+    // sumF (FP64) is current from the W half; sumW changed in it, so sum W again.
+    nmfkl_status st = launch_colsum(c, c->Wt, c->n, c->sumW, c->dsum[0]);
+    if (st != NMFKL_OK) return st;
+    const int tok = timer_begin(c, "objective_fused");
+    fused_objective_kernel<<<1, 1024, 0, c->stream>>>(c->unit_obj, c->n, c->dsum[0], c->dsum[1], c->p.r, c->dscalar);
+    timer_end(c, tok);
+    if (!cuda_ok(c, cudaGetLastError(), "fused objective")) return NMFKL_ECUDA;
+    double h = 0.0;
+    if (!cuda_ok(c, cudaMemcpyAsync(&h, c->dscalar, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy objective") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "objective sync"))
+        return NMFKL_ECUDA;
+    if (kl) *kl = h;
+    if (!std::isfinite(h)) {
         c->err = "objective is not finite";
         return NMFKL_ENUMERIC;
     }

@@ -79,6 +79,8 @@ struct HalfArgs {
     int32_t lcap;          // tile row length (max nonzeros of a unit in this bucket)
     unsigned long long *counters;  // coords, evals, steps, cap_hits
     int32_t *err;          // device error flag
+    double *unit_obj;      // if set: per unit, sum over its nonzeros of v log(v/(x+eps)) - v
+                           // at the unit's final x (Eq. 1's data term, fused into the W half)
 };
 
 // One launch configuration of the sweep kernel family.
@@ -86,6 +88,7 @@ struct Bucket {
     int kind;         // index into the kernel table
     int nt;           // threads per subproblem group (32 = one warp)
     int k;            // nonzeros per thread held in registers (0 = giant)
+    int cl;           // CTAs per cluster (1 = no cluster)
     int32_t count;    // units in the bucket
     int32_t lcap;     // tile row length
     int32_t *d_units; // device list of unit ids
@@ -122,6 +125,8 @@ struct nmfkl_ctx {
     // factors, unit-major with row stride ldr: Wt (n x ldr), Ft (m x ldr)
     float *Wt = nullptr, *Ft = nullptr;
     float *sumW = nullptr, *sumF = nullptr;
+    double *dsum[2] = {nullptr, nullptr};  // FP64 sumW (0) and sumF (1) of the last colsum
+    double *unit_obj = nullptr;            // n per-row data terms of the fused objective
     double *dpart = nullptr;       // reduction partials
     int64_t dpart_len = 0;
     double *dscalar = nullptr;     // small FP64 results
@@ -157,7 +162,8 @@ void free_plan(nmfkl_ctx *c);
 const char *kind_name(int kind);
 
 // aux.cu
-nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out);
+nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out, double *out_d);
+nmfkl_status launch_fused_objective(nmfkl_ctx *c, double *kl);
 nmfkl_status launch_objective(nmfkl_ctx *c, double *kl, double *reg);
 nmfkl_status launch_uniform_init(nmfkl_ctx *c, int which, float *X, int64_t cols);
 nmfkl_status launch_to_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols);

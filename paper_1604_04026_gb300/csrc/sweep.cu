@@ -18,6 +18,8 @@
 // plus for CTA groups one shared-memory exchange per evaluation.
 #include "common.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -138,8 +140,17 @@ __device__ __forceinline__ Staged stage_chunk32(const HalfArgs &a, float *tile, 
 // incremental updates is dropped; otherwise the value is kept >= 0.
 __device__ __forceinline__ float step_x(float x, float av, float d, int dc, int &terms) {
     x = fmaf(d, av, x);
+    if (dc == 0) return fmaxf(x, 0.f);  // no term appears or vanishes (dc is group-uniform)
     if (av > 0.f) terms += dc;
     return terms == 0 ? 0.f : fmaxf(x, 0.f);
+}
+
+// 1 / (x + eps) with the hardware approximation (relative error ~1 ulp;
+// x + eps >= eps > 0, so no denormal or zero input).
+__device__ __forceinline__ float recip(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 struct Tally {
@@ -151,6 +162,31 @@ __device__ __forceinline__ void flush_tally(const HalfArgs &a, const Tally &t) {
     if (t.evals) atomicAdd(&a.counters[1], t.evals);
     if (t.steps) atomicAdd(&a.counters[2], t.steps);
     if (t.caps) atomicAdd(&a.counters[3], t.caps);
+}
+
+// Drops the L2 lines of a finished tile (r rows of `len` floats, row stride
+// lcap) without writing them back: the tile is dead once its unit is done.
+// Whole 128-byte lines only; the partial lines at row ends are left alone.
+__device__ __forceinline__ void discard_tile(float *tile, int r, int len, int lcap, int tid, int nthreads) {
+    const int per_row = (len * 4) / 128;  // full lines from the row start (rows are 128-byte aligned)
+    if (per_row == 0 || (lcap * 4) % 128 != 0) return;
+    const int total = r * per_row;
+    for (int i = tid; i < total; i += nthreads) {
+        const int k = i / per_row, l = i - k * per_row;
+        const char *addr = reinterpret_cast<const char *>(tile + (int64_t)k * lcap) + 128 * l;
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(addr) : "memory");
+    }
+}
+
+// Eq. 1's data term of one nonzero at its final model value (FP32 term).
+__device__ __forceinline__ float kl_term(float v, float x, float eps_div) {
+    return v > 0.f ? v * logf(v / (x + eps_div)) - v : 0.f;
+}
+
+__device__ __forceinline__ double warp_sum_d(double t) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    return t;
 }
 
 // The projected Newton loop of Algorithm 2 for one coordinate. eval() returns
@@ -277,7 +313,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
                         xr[s] = x_l;
                         cr[s] = st.terms;
                         vr[s] = v_l;
-                        const float ri = __frcp_rn(x_l + eps_div);
+                        const float ri = recip(x_l + eps_div);
                         wr[s] = v_l * ri;
                         qr[s] = wr[s] * ri;
                     }
@@ -347,7 +383,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
                 for (int s = 0; s < K; ++s) {
                     if (s < ks) {
                         xr[s] = step_x(xr[s], ac[s], d, dc, cr[s]);
-                        const float ri = __frcp_rn(xr[s] + eps_div);
+                        const float ri = recip(xr[s] + eps_div);
                         wr[s] = vr[s] * ri;
                         qr[s] = wr[s] * ri;
                     }
@@ -360,7 +396,28 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
             process(acur, anxt, kk);
             if (kk + 1 < r) process(anxt, acur, kk + 1);
         }
+        if (a.unit_obj) {
+            float t = 0.f;
+#pragma unroll
+            for (int s = 0; s < K; ++s)
+                if (s < ks) t += kl_term(vr[s], xr[s], eps_div);
+            double dt = warp_sum_d((double)t);
+            if constexpr (kCta) {
+                double *rd = reinterpret_cast<double *>(red + parity * kNW);
+                if (lane == 0) rd[warp_in_block] = dt;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double tot = 0.0;
+                    for (int w = 0; w < kNW; ++w) tot += rd[w];
+                    a.unit_obj[u] = tot;
+                }
+                parity ^= 1;
+            } else if (lane == 0) {
+                a.unit_obj[u] = dt;
+            }
+        }
         if constexpr (kCta) __syncthreads(); else __syncwarp();
+        discard_tile(tile, r, L, lcap, tid_g, NT);
         for (int k = tid_g; k < r; k += NT) {
             const float xv = x_out[k];
             if (!(xv == xv)) atomicOr(a.err, 1);
@@ -423,7 +480,7 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
             const Staged st = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
             if (pl < L) {
                 const float x_l = st.terms == 0 ? 0.f : st.x;
-                const float ri = __frcp_rn(x_l + eps_div);
+                const float ri = recip(x_l + eps_div);
                 gc[pl] = st.terms;
                 gx[pl] = x_l;
                 gv[pl] = v_l;
@@ -471,7 +528,7 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
                     int terms = __ldcg(gc + p);
                     const float xv = step_x(__ldcg(gx + p), __ldcg(col + p), d, dc, terms);
                     gc[p] = terms;
-                    const float ri = __frcp_rn(xv + eps_div);
+                    const float ri = recip(xv + eps_div);
                     const float wv = __ldcg(gv + p) * ri;
                     gx[p] = xv;
                     gw[p] = wv;
@@ -480,6 +537,20 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
             };
             const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
             if (threadIdx.x == 0) x_out[k] = xk;
+        }
+        if (a.unit_obj) {
+            float t = 0.f;
+            for (int p = threadIdx.x; p < L; p += kGiantNT) t += kl_term(__ldcg(gv + p), __ldcg(gx + p), eps_div);
+            const double dt = warp_sum_d((double)t);
+            double *rd = reinterpret_cast<double *>(red + parity * kNW);
+            if (lane == 0) rd[warp] = dt;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < kNW; ++w) tot += rd[w];
+                a.unit_obj[u] = tot;
+            }
+            parity ^= 1;
         }
         __syncthreads();
         for (int k = threadIdx.x; k < r; k += kGiantNT) {
@@ -491,34 +562,333 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
     if (threadIdx.x == 0) flush_tally(a, tally);
 }
 
+
+// ---------------------------------------------------------------------------
+// Cluster groups: a unit too long for one CTA's registers is split across the
+// CL CTAs of a thread-block cluster (one CTA per SM). CTA c stages and owns
+// the contiguous slice [c*Lc, (c+1)*Lc) of the unit's nonzeros (Lc =
+// ceil(L / CL)) with K of them per thread in registers. Every evaluation
+// reduces inside the CTA, then exchanges the CTA partials through
+// distributed shared memory: each CTA stores its partial into slot[rank] of
+// every CTA of the cluster and arrives on that CTA's mbarrier; each CTA
+// waits on its own mbarrier (bounded by a clock limit: on timeout it sets
+// the error flag and every later exchange is skipped) and sums the slots in
+// rank order, so all CTAs hold identical totals and take identical Newton
+// decisions. Units are assigned to clusters round-robin, longest first.
+// ---------------------------------------------------------------------------
+constexpr int kClusterMax = 16;
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: a wait that long is a fault
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
+    return out;
+}
+__device__ __forceinline__ void st_cluster_u64(uint32_t addr, unsigned long long v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+template <int NT, int K>
+__global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const uint32_t crank = cluster.block_rank();
+    const uint32_t csize = cluster.num_blocks();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kNW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = a.r, ldr = a.ldr, S = odd_stride(r);
+    uint8_t *perm = smem_raw;
+    float *x_init = reinterpret_cast<float *>(smem_raw + 256);
+    float *x_out = x_init + ldr;
+    float *stg_base = reinterpret_cast<float *>(smem_raw + stage_offset(ldr));
+    float *stg = stg_base + warp * 8 * S;
+    float2 *red = reinterpret_cast<float2 *>(stg_base + kNW * 8 * S);
+    unsigned long long *slots = reinterpret_cast<unsigned long long *>(red + 2 * kNW);  // [2][kClusterMax]
+    unsigned long long *mbar = slots + 2 * kClusterMax;                                 // [2]
+    uint64_t *words = reinterpret_cast<uint64_t *>(stg_base);
+    __shared__ int s_abort;
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&mbar[0]), csize);
+        mbar_init(smem_addr(&mbar[1]), csize);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster.sync();
+
+    float *tile = a.scratch + (int64_t)blockIdx.x * a.slot_floats;
+    const int lcap = a.lcap;
+    const float eps_div = a.eps_div;
+    Tally tally;
+    int par = 0;
+    uint32_t phase[2] = {0u, 0u};
+    const int nclusters = gridDim.x / csize;
+    const int cid = blockIdx.x / csize;
+
+    // Sum of one 64-bit contribution per CTA of the cluster (rank order).
+    auto exchange = [&](unsigned long long mine, auto &&combine) {
+        if (warp == 0) {
+            const bool live = !s_abort;
+            const uint32_t my_bar = smem_addr(&mbar[par]);
+            if (live && lane < (int)csize) {
+                // lane c stores this CTA's partial into CTA c, then arrives there
+                const uint32_t my_slot = smem_addr(&slots[par * kClusterMax + crank]);
+                st_cluster_u64(map_rank(my_slot, lane), mine);
+                mbar_arrive_remote(map_rank(my_bar, lane));
+            }
+            if (live && lane == 0) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(my_bar, phase[par])) {
+                    if (clock64() - t0 > kWaitCycles) {
+                        s_abort = 1;
+                        atomicOr(a.err, 2);
+                        break;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        combine(slots + par * kClusterMax, csize);
+        phase[par] ^= 1u;
+        par ^= 1;
+    };
+
+    for (int qi = cid; qi < a.count; qi += nclusters) {
+        const int64_t u = a.units[qi];
+        const int64_t ubase = a.ptr[u];
+        const int Lall = (int)(a.ptr[u + 1] - ubase);
+        const int Lc = (Lall + (int)csize - 1) / (int)csize;
+        const int my0 = (int)crank * Lc;
+        const int L = max(0, min(Lc, Lall - my0));
+        const int64_t base = ubase + my0;
+        const int ks = (L + NT - 1) / NT;
+
+        for (int k = threadIdx.x; k < ldr; k += NT) x_init[k] = a.X[u * ldr + k];
+        __syncthreads();
+        float xr[K], vr[K], wr[K], qr[K];
+        int cr[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
+            if (s < ks) {
+                const int p0 = 32 * warp + NT * s;
+                if (p0 < L) {
+                    const int pl = p0 + lane;
+                    int idx_l = 0;
+                    float v_l = 0.f;
+                    if (pl < L) {
+                        idx_l = a.idx[base + pl];
+                        v_l = a.val[base + pl];
+                    }
+                    const Staged st = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
+                    if (pl < L) {
+                        const float x_l = st.terms == 0 ? 0.f : st.x;
+                        xr[s] = x_l;
+                        cr[s] = st.terms;
+                        vr[s] = v_l;
+                        const float ri = recip(x_l + eps_div);
+                        wr[s] = v_l * ri;
+                        qr[s] = wr[s] * ri;
+                    }
+                }
+            }
+        }
+        if (warp == 0) {
+            ids_words_warp(words, r, u, a.sweep, a.side, a.perm_mode, a.seed, lane);
+            __syncwarp();
+            if (lane == 0) fisher_yates(perm, words, r);
+            __syncwarp();
+        }
+        __syncthreads();
+
+        auto load_col = [&](float (&dst)[K], int k) {
+            const float *col = tile + (int64_t)k * lcap;
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                const int p = threadIdx.x + NT * s;
+                dst[s] = (s < ks && p < L) ? __ldcg(col + p) : 0.f;
+            }
+        };
+        auto reduce = [&](float sg, float sh) -> float2 {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sg += __shfl_xor_sync(kFull, sg, o);
+                sh += __shfl_xor_sync(kFull, sh, o);
+            }
+            float2 *rb = red + par * kNW;
+            if (lane == 0) rb[warp] = make_float2(sg, sh);
+            __syncthreads();
+            float tg = 0.f, th = 0.f;
+#pragma unroll
+            for (int w = 0; w < kNW; ++w) {
+                const float2 v = rb[w];
+                tg += v.x;
+                th += v.y;
+            }
+            float2 tot = make_float2(0.f, 0.f);
+            const float2 mine = make_float2(tg, th);
+            exchange(*reinterpret_cast<const unsigned long long *>(&mine),
+                     [&](const unsigned long long *sl, uint32_t n) {
+                         for (uint32_t c = 0; c < n; ++c) {
+                             const float2 v = *reinterpret_cast<const float2 *>(&sl[c]);
+                             tot.x += v.x;
+                             tot.y += v.y;
+                         }
+                     });
+            return tot;
+        };
+
+        float acur[K], anxt[K];
+        load_col(acur, perm[0]);
+        auto process = [&](float (&ac)[K], float (&an)[K], int kk) {
+            const int k = perm[kk];
+            if (kk + 1 < r) load_col(an, perm[kk + 1]);
+            auto eval = [&]() -> float2 {
+                float sg = 0.f, sh = 0.f;
+#pragma unroll
+                for (int s = 0; s < K; ++s) {
+                    if (s < ks) {
+                        sg = fmaf(wr[s], ac[s], sg);
+                        sh = fmaf(qr[s] * ac[s], ac[s], sh);
+                    }
+                }
+                return reduce(sg, sh);
+            };
+            auto update = [&](float d, int dc) {
+#pragma unroll
+                for (int s = 0; s < K; ++s) {
+                    if (s < ks) {
+                        xr[s] = step_x(xr[s], ac[s], d, dc, cr[s]);
+                        const float ri = recip(xr[s] + eps_div);
+                        wr[s] = vr[s] * ri;
+                        qr[s] = wr[s] * ri;
+                    }
+                }
+            };
+            const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+            if (threadIdx.x == 0) x_out[k] = xk;
+        };
+        for (int kk = 0; kk < r; kk += 2) {
+            process(acur, anxt, kk);
+            if (kk + 1 < r) process(anxt, acur, kk + 1);
+        }
+        if (a.unit_obj) {
+            float t = 0.f;
+#pragma unroll
+            for (int s = 0; s < K; ++s)
+                if (s < ks) t += kl_term(vr[s], xr[s], eps_div);
+            const double dt = warp_sum_d((double)t);
+            double *rd = reinterpret_cast<double *>(red + par * kNW);
+            if (lane == 0) rd[warp] = dt;
+            __syncthreads();
+            double cta = 0.0;
+            for (int w = 0; w < kNW; ++w) cta += rd[w];
+            double tot = 0.0;
+            exchange(static_cast<unsigned long long>(__double_as_longlong(cta)),
+                     [&](const unsigned long long *sl, uint32_t n) {
+                         for (uint32_t c = 0; c < n; ++c) tot += __longlong_as_double(static_cast<long long>(sl[c]));
+                     });
+            if (crank == 0 && threadIdx.x == 0) a.unit_obj[u] = tot;
+        }
+        __syncthreads();
+        discard_tile(tile, r, L, lcap, threadIdx.x, NT);
+        if (crank == 0) {
+            for (int k = threadIdx.x; k < r; k += NT) {
+                const float xv = x_out[k];
+                if (!(xv == xv)) atomicOr(a.err, 1);
+                a.X[u * ldr + k] = xv;
+            }
+        }
+    }
+    if (crank == 0 && threadIdx.x == 0) flush_tally(a, tally);
+    // no CTA may leave while a peer can still write into its shared memory
+    cluster.sync();
+}
+
 // ---------------------------------------------------------------------------
 // Host side: the bucket table and the plan.
 // ---------------------------------------------------------------------------
 struct KernelKind {
     const void *fn;
-    int nt, k;
+    int nt, k, cl;  // threads per CTA (32: warp groups), nonzeros per thread, CTAs per cluster
     const char *name;
 };
 
+constexpr int kClusterNT = 512, kClusterK = 12;
 const KernelKind kKinds[] = {
-    {(const void *)sweep_kernel<32, 1>, 32, 1, "sweep_warp_k1"},
-    {(const void *)sweep_kernel<32, 2>, 32, 2, "sweep_warp_k2"},
-    {(const void *)sweep_kernel<32, 4>, 32, 4, "sweep_warp_k4"},
-    {(const void *)sweep_kernel<32, 8>, 32, 8, "sweep_warp_k8"},
-    {(const void *)sweep_kernel<32, 16>, 32, 16, "sweep_warp_k16"},
-    {(const void *)sweep_kernel<128, 8>, 128, 8, "sweep_cta128_k8"},
-    {(const void *)sweep_kernel<256, 8>, 256, 8, "sweep_cta256_k8"},
-    {(const void *)sweep_kernel<512, 8>, 512, 8, "sweep_cta512_k8"},
-    {(const void *)sweep_kernel<512, 16>, 512, 16, "sweep_cta512_k16"},
-    {(const void *)sweep_giant_kernel, kGiantNT, 0, "sweep_giant"},
+    {(const void *)sweep_kernel<32, 1>, 32, 1, 1, "sweep_warp_k1"},
+    {(const void *)sweep_kernel<32, 2>, 32, 2, 1, "sweep_warp_k2"},
+    {(const void *)sweep_kernel<32, 4>, 32, 4, 1, "sweep_warp_k4"},
+    {(const void *)sweep_kernel<32, 8>, 32, 8, 1, "sweep_warp_k8"},
+    {(const void *)sweep_kernel<32, 16>, 32, 16, 1, "sweep_warp_k16"},
+    {(const void *)sweep_kernel<128, 8>, 128, 8, 1, "sweep_cta128_k8"},
+    {(const void *)sweep_kernel<256, 8>, 256, 8, 1, "sweep_cta256_k8"},
+    {(const void *)sweep_kernel<512, 8>, 512, 8, 1, "sweep_cta512_k8"},
+    {(const void *)sweep_kernel<512, 16>, 512, 16, 1, "sweep_cta512_k16"},
+    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK>, kClusterNT, kClusterK, 2, "sweep_cluster2"},
+    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK>, kClusterNT, kClusterK, 4, "sweep_cluster4"},
+    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK>, kClusterNT, kClusterK, 8, "sweep_cluster8"},
+    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK>, kClusterNT, kClusterK, 16, "sweep_cluster16"},
+    {(const void *)sweep_giant_kernel, kGiantNT, 0, 1, "sweep_giant"},
 };
 constexpr int kNumKinds = sizeof(kKinds) / sizeof(kKinds[0]);
 constexpr int kGiantKind = kNumKinds - 1;
 
-int kind_for_length(int64_t L) {
+// First usable kind whose capacity holds L (giant beyond every capacity).
+int kind_for_length(int64_t L, const std::vector<char> &usable) {
     for (int i = 0; i < kGiantKind; ++i)
-        if (L <= (int64_t)kKinds[i].nt * kKinds[i].k) return i;
+        if (usable[i] && L <= (int64_t)kKinds[i].nt * kKinds[i].k * kKinds[i].cl) return i;
     return kGiantKind;
+}
+
+size_t cluster_smem_bytes(int r, int ldr) {
+    return group_smem_bytes(r, ldr, kClusterNT / 32, true) + (2 * kClusterMax + 2) * sizeof(unsigned long long);
+}
+
+// Clusters of `cl` CTAs of the cluster kernel that fit on the device at once.
+int active_clusters(int cl, size_t smem) {
+    const void *fn = kKinds[kGiantKind - 1].fn;
+    if (cl > 8) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(kClusterNT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 }  // namespace
@@ -540,11 +910,19 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
     if (!cuda_ok(c, cudaMemcpy(ptr.data(), dptr, sizeof(int64_t) * (units + 1), cudaMemcpyDeviceToHost),
                  "copy offsets"))
         return NMFKL_ECUDA;
+    const int r0 = c->p.r, ldr0 = c->ldr;
+    std::vector<char> usable(kNumKinds, 1);
+    std::vector<int> clusters_fit(kNumKinds, 0);
+    for (int kind = 0; kind < kGiantKind; ++kind) {
+        if (kKinds[kind].cl <= 1) continue;
+        clusters_fit[kind] = active_clusters(kKinds[kind].cl, cluster_smem_bytes(r0, ldr0));
+        usable[kind] = clusters_fit[kind] > 0;
+    }
     std::vector<std::vector<int32_t>> lists(kNumKinds);
     std::vector<int64_t> maxlen(kNumKinds, 0), nnz(kNumKinds, 0);
     for (int64_t u = 0; u < units; ++u) {
         const int64_t L = ptr[u + 1] - ptr[u];
-        const int kind = kind_for_length(L);
+        const int kind = kind_for_length(L, usable);
         lists[kind].push_back((int32_t)u);
         maxlen[kind] = std::max(maxlen[kind], L);
         nnz[kind] += L;
@@ -566,6 +944,24 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
         b.count = (int32_t)lst.size();
         b.max_len = maxlen[kind];
         b.nnz = nnz[kind];
+        b.cl = kKinds[kind].cl;
+        if (b.cl > 1) {
+            b.block = b.nt;
+            b.smem = cluster_smem_bytes(r, ldr);
+            const int nclu = (int)std::min<int64_t>(b.count, clusters_fit[kind]);
+            b.grid = nclu * b.cl;
+            b.groups = b.grid;
+            b.lcap = b.nt * b.k;
+            b.slot_floats = ((int64_t)r * b.lcap + 63) / 64 * 64;
+            if (!cuda_ok(c, cudaMalloc(&b.d_units, sizeof(int32_t) * lst.size()), "alloc unit list"))
+                return NMFKL_ENOMEM;
+            if (!cuda_ok(c, cudaMemcpy(b.d_units, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice),
+                         "copy unit list"))
+                return NMFKL_ECUDA;
+            c->plan[side].push_back(b);
+            c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
+            continue;
+        }
         const bool cta = b.nt > 32;
         const int warps = b.nt / 32;
         const size_t gbytes = group_smem_bytes(r, ldr, cta ? warps : 1, cta);
@@ -620,7 +1016,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
     const float *At = F ? c->Wt : c->Ft;
     float *X = F ? c->Ft : c->Wt;
     float *sumA = F ? c->sumW : c->sumF;
-    nmfkl_status st = launch_colsum(c, At, F ? c->n : c->m, sumA);
+    nmfkl_status st = launch_colsum(c, At, F ? c->n : c->m, sumA, c->dsum[F ? 0 : 1]);
     if (st != NMFKL_OK) return st;
     HalfArgs a{};
     a.ptr = F ? c->colptr : c->rowptr;
@@ -646,6 +1042,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
     a.scratch = c->scratch;
     a.counters = c->counters;
     a.err = c->err_flag;
+    a.unit_obj = F ? nullptr : c->unit_obj;
     int qi = 0;
     for (auto &b : c->plan[side]) {
         a.units = b.d_units;
@@ -657,7 +1054,24 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
             return NMFKL_ECUDA;
         void *args[] = {&a};
         const int tok = timer_begin(c, kKinds[b.kind].name);
-        cudaError_t e = cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, c->stream);
+        cudaError_t e;
+        if (b.cl > 1) {
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(b.grid);
+            cfg.blockDim = dim3(b.block);
+            cfg.dynamicSmemBytes = b.smem;
+            cfg.stream = c->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = b.cl;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelExC(&cfg, kKinds[b.kind].fn, args);
+        } else {
+            e = cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, c->stream);
+        }
         timer_end(c, tok);
         if (!cuda_ok(c, e, kKinds[b.kind].name)) return NMFKL_ECUDA;
     }

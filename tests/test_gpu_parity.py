@@ -339,3 +339,35 @@ def test_invalid_arguments(torch):
     with pytest.raises(nk.NMFKLError, match="EINVAL"):
         m.set_data(nnz=3, colptr=good_ptr, rowidx=bad, val=v, rowptr=rp, colidx=ci, rval=v)
     m.close()
+
+
+def test_long_rows_every_cluster_size():
+    """Rows of 9k..99k nonzeros: CTA, cluster-of-2/4/8/16 and (beyond) giant
+    kernels on the W half, against the oracle from an identical state."""
+    rng = np.random.default_rng(4)
+    n, m = 64, 100_000
+    lens = [9_000, 13_000, 20_000, 30_000, 45_000, 60_000, 80_000, 99_000]
+    rows, cols = [], []
+    for i, L in enumerate(lens):
+        c = np.sort(rng.choice(m, size=L, replace=False))
+        rows.append(np.full(L, i)); cols.append(c)
+    extra = rng.integers(0, m, size=4 * m)
+    rows.append(rng.integers(len(lens), n, size=extra.size)); cols.append(extra)
+    R = np.concatenate(rows); C = np.concatenate(cols)
+    key = np.unique(C.astype(np.int64) * n + R)
+    C, R = key // n, key % n
+    colptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(C, minlength=m), out=colptr[1:])
+    V = synth.from_csc(n, m, colptr, R.astype(np.int32), rng.integers(1, 6, size=R.size).astype(np.float32))
+    r = 12
+    W0, F0 = start(V, r, seed=3)
+    p = params(r, seed=8, **TIGHT)
+    m_ = model(V, W0, F0, p)
+    kinds = {b["kernel"] for b in m_.plan() if b["side"] == 1}
+    assert any(k.startswith("sweep_cluster") for k in kinds), kinds
+    m_.sweep_W(0)
+    Wg = m_.get_W()
+    m_.close()
+    Wo, _ = oracle.half_W(V, W0, F0, 8, 0, cfg_for(p, 1), threads=8)
+    dev, _ = fp32_sensitivity(V, W0, F0, 1, p, Wo)
+    assert within(Wg, Wo, slack=PROBE_FACTOR * dev).all()
