@@ -191,6 +191,42 @@ int32_t nmfkl_plan_info(const nmfkl_ctx *ctx, nmfkl_bucket_info *out, int32_t ca
 nmfkl_status nmfkl_debug_perm(nmfkl_ctx *ctx, int64_t sweep, int32_t side, int64_t count,
                               const int64_t *cols, int32_t *out);
 
+/* F half without any allocation.
+ *
+ * The paper has no counterpart: this is for callers that cannot call
+ * cudaMalloc -- code running while another runtime owns the device memory
+ * through its own pool (a new allocation would fail or fragment that pool),
+ * code on a latency-critical path where cudaMalloc's implicit device-wide
+ * synchronization is not acceptable, and code that must not fail with an
+ * out-of-memory error after start-up. It allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine); its scratch is one 32 MiB array
+ * with static storage in the library, which every GPU that loads the
+ * library holds until the process exits.
+ *
+ * Does what nmfkl_sweep_F does for one F half (sumW = W 1, then Algorithm 2
+ * on every column with ids(seed, sweep, side 0, column)), on buffers the
+ * caller owns, all device memory of the current device:
+ *   colptr int64[m+1], rowidx int32[nnz], val float[nnz]: CSC of V (n x m),
+ *     indices sorted, values > 0;
+ *   Wt float[n * ldr]: W unit-major (row i holds W[0..r-1, i]), ldr =
+ *     4 * ceil(r / 4), padding entries 0;
+ *   Ft float[m * ldr]: F unit-major, read as the start and overwritten.
+ * Parameters as in nmfkl_params (side F: alpha_F, beta_F). max_len bounds
+ * the nonzeros of every column; limits: r <= 256 and max_len <= 256 (EINVAL
+ * beyond them; a column longer than max_len is reported as EINVAL after the
+ * launch and left unchanged). Synchronizes `stream` (a cudaStream_t or NULL)
+ * to read its error flags.
+ *
+ * The first call on a device takes the scratch array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture. Every call shares the one array and leaves its
+ * contents behind; the work counter it needs at zero is cleared at the start
+ * of each call. Calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on the scratch and must be serialized by the caller. */
+nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, int64_t m, int32_t max_len,
+                                   const int64_t *colptr, const int32_t *rowidx, const float *val,
+                                   const float *Wt, float *Ft, int64_t sweep, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

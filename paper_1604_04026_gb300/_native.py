@@ -53,6 +53,8 @@ SIGNATURES = [
     ("nmfkl_set_timing", c_i32, [c_vp, c_i32]),
     ("nmfkl_kernel_times", c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32]),
     ("nmfkl_debug_perm", c_i32, [c_vp, c_i64, c_i32, c_i64, c_vp, c_vp]),
+    ("nmfkl_sweep_F_noalloc", c_i32, [ctypes.POINTER(Params), c_i64, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp,
+                                      c_vp, c_i64, c_vp]),
 ]
 
 _lib = None

@@ -270,6 +270,12 @@ __global__ void fused_objective_kernel(const double *unit_obj, int64_t n, const 
     }
 }
 
+void launch_colsum_raw(cudaStream_t stream, const float *At, int64_t rows, int ldr, int r, double *part,
+                       float *out, double *out_d) {
+    colsum_partial_kernel<<<kColsumBlocks, 256, 0, stream>>>(At, rows, ldr, part);
+    colsum_final_kernel<<<1, 256, 0, stream>>>(part, kColsumBlocks, ldr, r, out, out_d);
+}
+
 nmfkl_status launch_fused_objective(nmfkl_ctx *c, double *kl) {
     // sumF (FP64) is current from the W half; sumW changed in it, so sum W again.
     nmfkl_status st = launch_colsum(c, c->Wt, c->n, c->sumW, c->dsum[0]);

@@ -164,6 +164,9 @@ const char *kind_name(int kind);
 // aux.cu
 nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out, double *out_d);
 nmfkl_status launch_fused_objective(nmfkl_ctx *c, double *kl);
+// colsum into caller buffers: part holds 1024 x ldr doubles.
+void launch_colsum_raw(cudaStream_t stream, const float *At, int64_t rows, int ldr, int r, double *part,
+                       float *out, double *out_d);
 nmfkl_status launch_objective(nmfkl_ctx *c, double *kl, double *reg);
 nmfkl_status launch_uniform_init(nmfkl_ctx *c, int which, float *X, int64_t cols);
 nmfkl_status launch_to_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols);

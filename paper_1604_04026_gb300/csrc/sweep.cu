@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 namespace nmfkl {
 
@@ -239,7 +240,7 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
 // Register-resident groups: NT threads (32 = one warp per subproblem, several
 // per block; otherwise one CTA), K nonzeros per thread, so L <= NT*K.
 // ---------------------------------------------------------------------------
-template <int NT, int K>
+template <int NT, int K, bool kFree = false>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
@@ -283,9 +284,16 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
             qi = __shfl_sync(kFull, q, 0);
         }
         if (qi >= a.count) break;
-        const int64_t u = a.units[qi];
+        const int64_t u = kFree ? (int64_t)qi : (int64_t)a.units[qi];
         const int64_t base = a.ptr[u];
         const int L = (int)(a.ptr[u + 1] - base);
+        if constexpr (kFree) {
+            // no length buckets on this path: a unit beyond NT*K nonzeros is refused
+            if (L > NT * K || L < 0) {
+                if (tid_g == 0) atomicOr(a.err, 4);
+                continue;
+            }
+        }
         const int ks = (L + NT - 1) / NT;
 
         for (int k = tid_g; k < ldr; k += NT) x_init[k] = a.X[u * ldr + k];
@@ -1075,6 +1083,143 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
         timer_end(c, tok);
         if (!cuda_ok(c, e, kKinds[b.kind].name)) return NMFKL_ECUDA;
     }
+    return NMFKL_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free F half (nmfkl_sweep_F_noalloc in include/nmfkl.h).
+//
+// Its scratch is the file-scope array below, held by every GPU that loads
+// this library until the process exits:
+//   [0, 2 MiB)        colsum partials (1024 blocks x up to 256 doubles)
+//   [2 MiB, +4 KiB)   control: work counter, error flags, work counters,
+//                     sumW (FP32 and FP64)
+//   [2 MiB + 4 KiB, 32 MiB)  per-warp tiles (32*K x r floats each)
+// Host code cannot use the array's name as a device address, so the address
+// is taken with cudaGetSymbolAddress once per device (with that device
+// current) on the first call there, and passed to the kernels.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocBytes = size_t(32) << 20;
+constexpr size_t kNoAllocPartBytes = size_t(2) << 20;
+constexpr size_t kNoAllocCtlBytes = 4096;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+struct NoAllocCtl {  // lives at the start of the control block
+    int32_t queue;
+    int32_t err;
+    unsigned long long counters[4];
+};
+
+const KernelKind kFreeKinds[] = {
+    {(const void *)sweep_kernel<32, 1, true>, 32, 1, 1, "sweep_warp_k1_noalloc"},
+    {(const void *)sweep_kernel<32, 2, true>, 32, 2, 1, "sweep_warp_k2_noalloc"},
+    {(const void *)sweep_kernel<32, 4, true>, 32, 4, 1, "sweep_warp_k4_noalloc"},
+    {(const void *)sweep_kernel<32, 8, true>, 32, 8, 1, "sweep_warp_k8_noalloc"},
+};
+}  // namespace
+
+extern "C" nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, int64_t m, int32_t max_len,
+                                              const int64_t *colptr, const int32_t *rowidx, const float *val,
+                                              const float *Wt, float *Ft, int64_t sweep, void *stream) {
+    if (!p || p->r < 1 || p->r > kMaxR || n < 1 || m < 1 || n > INT32_MAX || m > INT32_MAX || max_len < 0 ||
+        max_len > 256 || !colptr || !Wt || !Ft || (max_len > 0 && (!rowidx || !val)))
+        return NMFKL_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return NMFKL_ECUDA;
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return NMFKL_ECUDA;
+            }
+            g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int r = p->r, ldr = (r + 3) / 4 * 4;
+    double *part = reinterpret_cast<double *>(base);
+    unsigned char *ctl_bytes = base + kNoAllocPartBytes;
+    NoAllocCtl *ctl = reinterpret_cast<NoAllocCtl *>(ctl_bytes);
+    float *sumW = reinterpret_cast<float *>(ctl_bytes + 256);
+    double *sumW_d = reinterpret_cast<double *>(ctl_bytes + 256 + 4 * kMaxR);
+    float *tiles = reinterpret_cast<float *>(base + kNoAllocPartBytes + kNoAllocCtlBytes);
+    const size_t tile_bytes = kNoAllocBytes - kNoAllocPartBytes - kNoAllocCtlBytes;
+
+    int kind = 0;
+    while (kind < 3 && max_len > 32 * kFreeKinds[kind].k) ++kind;
+    const KernelKind &kk = kFreeKinds[kind];
+    const int lcap = 32 * kk.k;
+    const int64_t slot_floats = ((int64_t)r * lcap + 63) / 64 * 64;
+    int optin = 0, sms = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    optin -= 1024;
+    const size_t gbytes = group_smem_bytes(r, ldr, 1, false);
+    int gpb = 8;
+    while (gpb > 1 && gbytes * gpb > (size_t)optin) --gpb;
+    const size_t smem = gbytes * gpb;
+    if (cudaFuncSetAttribute(kk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return NMFKL_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kk.fn, 32 * gpb, smem) != cudaSuccess || per_sm < 1)
+        return NMFKL_ECUDA;
+    const int64_t slots = (int64_t)(tile_bytes / sizeof(float)) / slot_floats;
+    const int64_t blocks_fit = slots / gpb;
+    const int64_t grid = std::min<int64_t>(std::min<int64_t>((m + gpb - 1) / gpb, (int64_t)per_sm * sms), blocks_fit);
+    if (grid < 1) return NMFKL_EINVAL;
+
+    if (cudaMemsetAsync(ctl_bytes, 0, sizeof(NoAllocCtl), st) != cudaSuccess) return NMFKL_ECUDA;
+    launch_colsum_raw(st, Wt, n, ldr, r, part, sumW, sumW_d);
+
+    HalfArgs a{};
+    a.ptr = colptr;
+    a.idx = rowidx;
+    a.val = val;
+    a.At = Wt;
+    a.X = Ft;
+    a.sumA = sumW;
+    a.r = r;
+    a.ldr = ldr;
+    a.alpha = (float)p->alpha_F;
+    a.beta = (float)p->beta_F;
+    a.eps_grad = (float)p->eps_grad;
+    a.eps_div = (float)p->eps_div;
+    a.eps_x = (float)p->eps_x;
+    a.max_inner = p->max_inner;
+    a.grad_mode = p->grad_mode;
+    a.break_mode = p->break_mode;
+    a.perm_mode = p->perm_mode;
+    a.seed = p->seed;
+    a.sweep = sweep;
+    a.side = 0;
+    a.units = nullptr;
+    a.count = (int32_t)m;
+    a.queue = &ctl->queue;
+    a.scratch = tiles;
+    a.slot_floats = slot_floats;
+    a.lcap = lcap;
+    a.counters = ctl->counters;
+    a.err = &ctl->err;
+    a.unit_obj = nullptr;
+    void *args[] = {&a};
+    if (cudaLaunchKernel(kk.fn, dim3((unsigned)grid), dim3(32 * gpb), args, smem, st) != cudaSuccess)
+        return NMFKL_ECUDA;
+    int32_t err = 0;
+    if (cudaMemcpyAsync(&err, &ctl->err, sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return NMFKL_ECUDA;
+    if (err & 4) return NMFKL_EINVAL;
+    if (err & 1) return NMFKL_ENUMERIC;
     return NMFKL_OK;
 }
 
