@@ -133,10 +133,12 @@ typedef struct {
                               probe (Parker 1997): [Ax]_p is multiplied by
                               (1 + perturb*xi), xi ~ U(-1, 1), after every update,
                               and by (1 + sqrt(r)*perturb*xi) after the initial sum,
-                              to measure how far rounding of x at that relative level
+                              keeping [Ax]_p >= 0 and exactly 0 when all its terms
+                              A_pk x_k are 0 (it is a sum of nonnegative terms), to
+                              measure how far rounding of x at that relative level
                               moves each result (tests use perturb = 2^-24, FP32's
                               unit roundoff). */
-    uint64_t perturb_seed; /* stream of the probe; each unit mixes in its index */
+    uint64_t perturb_seed; /* stream of the probe; each unit mixes in its index, sweep and side */
 } oracle_cfg;
 
 typedef struct {
@@ -175,12 +177,20 @@ static double probe_xi(uint64_t *state) {
 void oracle_alg2(int64_t L, const double *v, const double *A, const double *sumA, double *x,
                  int32_t r, const int32_t *ids, const oracle_cfg *c, double *Ax, oracle_stats *st) {
     uint64_t probe = c->perturb_seed;
+    /* Probe only: the number of positive terms A_pk x_k of each [Ax]_p. [Ax]_p
+     * is a sum of nonnegative terms, so it is exactly 0 when that count is 0
+     * and never negative; the perturbed values keep both properties. */
+    int32_t *terms = NULL;
+    if (c->perturb > 0.0) terms = (int32_t *)calloc((size_t)(L > 0 ? L : 1), sizeof(int32_t));
     /* Compute Ax on the nonzeros (Algorithm 2, first step). */
     for (int64_t p = 0; p < L; ++p) {
         double s = 0.0;
         for (int32_t k = 0; k < r; ++k) s += A[p * r + k] * x[k];
         Ax[p] = s;
-        if (c->perturb > 0.0) Ax[p] *= 1.0 + sqrt((double)r) * c->perturb * probe_xi(&probe);
+        if (terms) {
+            for (int32_t k = 0; k < r; ++k) terms[p] += (A[p * r + k] > 0.0 && x[k] > 0.0);
+            Ax[p] = terms[p] == 0 ? 0.0 : Ax[p] * (1.0 + sqrt((double)r) * c->perturb * probe_xi(&probe));
+        }
     }
     for (int32_t kk = 0; kk < r; ++kk) {
         int32_t k = ids[kk];
@@ -198,8 +208,18 @@ void oracle_alg2(int64_t L, const double *v, const double *A, const double *sumA
             else xn = g > 0.0 ? 0.0 : x[k];
             double dx = xn - x[k];
             for (int64_t p = 0; p < L; ++p) Ax[p] += dx * A[p * r + k];
-            if (c->perturb > 0.0)
-                for (int64_t p = 0; p < L; ++p) Ax[p] *= 1.0 + c->perturb * probe_xi(&probe);
+            if (terms) {
+                const double xnew = x[k] + dx;
+                const int dc = (x[k] == 0.0 && xnew > 0.0) ? 1 : ((x[k] > 0.0 && xnew == 0.0) ? -1 : 0);
+                for (int64_t p = 0; p < L; ++p) {
+                    if (A[p * r + k] > 0.0) terms[p] += dc;
+                    if (terms[p] == 0) Ax[p] = 0.0;
+                    else {
+                        Ax[p] *= 1.0 + c->perturb * probe_xi(&probe);
+                        if (Ax[p] < 0.0) Ax[p] = 0.0;
+                    }
+                }
+            }
             double xs = x[k];
             x[k] = x[k] + dx;
             if (st) st->steps++;
@@ -209,6 +229,7 @@ void oracle_alg2(int64_t L, const double *v, const double *A, const double *sumA
             if (st) st->evals++;
         }
     }
+    free(terms);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -257,7 +278,8 @@ static void *half_worker(void *arg) {
         for (int32_t k = 0; k < r; ++k) x[k] = J->X[(int64_t)k * J->nx + u];
         oracle_perm(J->seed, J->sweep, J->side, u, J->cfg->perm_mode, r, ids);
         oracle_cfg cu = *J->cfg;
-        cu.perturb_seed = J->cfg->perturb_seed ^ ((uint64_t)u * 0xD1B54A32D192ED03ULL);
+        cu.perturb_seed = J->cfg->perturb_seed ^ ((uint64_t)u * 0xD1B54A32D192ED03ULL) ^
+                          ((uint64_t)(J->sweep + 1) * 0x9E3779B97F4A7C15ULL) ^ ((uint64_t)J->side << 62);
         oracle_alg2(L, v, A, J->sumA, x, r, ids, &cu, Ax, &J->st);
         for (int32_t k = 0; k < r; ++k) J->X[(int64_t)k * J->nx + u] = x[k];
     }

@@ -304,6 +304,12 @@ nmfkl_status nmfkl_set_data(nmfkl_ctx *c, int64_t nnz, const int64_t *colptr, co
         free_data(c);
         return NMFKL_ENOMEM;
     }
+    // tiles only ever hold finite factor values; start them at 0
+    if (c->scratch_floats > 0 &&
+        !cuda_ok(c, cudaMemset(c->scratch, 0, sizeof(float) * (size_t)c->scratch_floats), "zero scratch")) {
+        free_data(c);
+        return NMFKL_ECUDA;
+    }
     c->have_data = true;
     return NMFKL_OK;
 }

@@ -70,69 +70,12 @@ __device__ __forceinline__ void ids_words_warp(uint64_t *words, int r, int64_t u
     }
 }
 
-// Stages the 32 nonzeros p0..p0+31 of a unit (one warp): loads their A rows,
-// writes them transposed into the tile and returns, in lane l, x_p of
-// nonzero p0 + l (0 if p0 + l >= L) and the number of coordinates with
-// A_pk > 0 and x_k > 0 (the positive terms of x_p). idx_l is the lane's own
-// row index.
+// x_p and the number of coordinates with A_pk > 0 and x_k > 0 (the positive
+// terms of x_p) for one staged nonzero.
 struct Staged {
     float x;
     int terms;
 };
-__device__ __forceinline__ Staged stage_chunk32(const HalfArgs &a, float *tile, float *stg, const float *x_init,
-                                                int p0, int L, int idx_l, int lane) {
-    const int r = a.r, ldr = a.ldr, S = odd_stride(r), lcap = a.lcap;
-    const int nf4 = ldr >> 2;
-    const int items = 8 * nf4;
-    float myx = 0.f;
-    int myc = 0;
-    for (int q = 0; q < 4; ++q) {
-        if (p0 + 8 * q >= L) break;  // warp-uniform
-        for (int b0 = 0; b0 < items; b0 += 32) {
-            const int it = b0 + lane;
-            const int row = it / nf4, f = it - row * nf4;
-            const int ridx = __shfl_sync(kFull, idx_l, 8 * q + (row & 7));
-            const int p = p0 + 8 * q + row;
-            if (it < items && p < L) {
-                const float4 v4 = __ldg(reinterpret_cast<const float4 *>(a.At + (int64_t)ridx * ldr) + f);
-                float *dst = stg + row * S + 4 * f;
-                if (4 * f + 0 < r) dst[0] = v4.x;
-                if (4 * f + 1 < r) dst[1] = v4.y;
-                if (4 * f + 2 < r) dst[2] = v4.z;
-                if (4 * f + 3 < r) dst[3] = v4.w;
-            }
-        }
-        __syncwarp();
-        {
-            const int row = lane >> 2, part = lane & 3;
-            float acc = 0.f;
-            int cnt = 0;
-            for (int k = part; k < r; k += 4) {
-                const float av = stg[row * S + k], xv = x_init[k];
-                acc = fmaf(av, xv, acc);
-                cnt += (av > 0.f && xv > 0.f);
-            }
-            acc += __shfl_xor_sync(kFull, acc, 1);
-            acc += __shfl_xor_sync(kFull, acc, 2);
-            cnt += __shfl_xor_sync(kFull, cnt, 1);
-            cnt += __shfl_xor_sync(kFull, cnt, 2);
-            const int li = lane - 8 * q;
-            const float got = __shfl_sync(kFull, acc, 4 * (li & 7));
-            const int gotc = __shfl_sync(kFull, cnt, 4 * (li & 7));
-            if (li >= 0 && li < 8) {
-                myx = got;
-                myc = gotc;
-            }
-        }
-        for (int kb = 0; kb < r; kb += 4) {
-            const int k = kb + (lane >> 3), i = lane & 7;
-            const int p = p0 + 8 * q + i;
-            if (k < r && p < L) tile[(int64_t)k * lcap + p] = stg[i * S + k];
-        }
-        __syncwarp();
-    }
-    return Staged{myx, myc};
-}
 
 // x_p after a step of coordinate k: x_p + d A_pk, where `dc` (+1, -1 or 0)
 // records whether x_k just became positive or just became zero. x_p is a
@@ -152,6 +95,42 @@ __device__ __forceinline__ float recip(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Stages nonzero p (one per lane; `valid` false for lanes past the unit's
+// end): streams the lane's A row (ldr floats, 16 bytes at a time),
+// accumulates x_p = sum_k A_pk x_k and the number of positive terms
+// (xpos[k] = 1 where x_k > 0), and writes the row into the tile transposed:
+// for each k the warp's 32 lanes store 32 consecutive entries of row k.
+__device__ __forceinline__ Staged stage_lane(const HalfArgs &a, float *tile, const float *x_init, const int *xpos,
+                                             int p, bool valid, int idx) {
+    const int r = a.r, nf4 = a.ldr >> 2;
+    const int64_t lcap = a.lcap;
+    const float4 *row = reinterpret_cast<const float4 *>(a.At + (int64_t)idx * a.ldr);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x_init);
+    const int4 *p4 = reinterpret_cast<const int4 *>(xpos);
+    float *tcol = tile + p;
+    float acc = 0.f;
+    int cnt = 0;
+    for (int f = 0; f < nf4; ++f) {
+        const float4 av = valid ? __ldg(row + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 xv = x4[f];
+        const int4 pv = p4[f];
+        acc = fmaf(av.x, xv.x, acc);
+        acc = fmaf(av.y, xv.y, acc);
+        acc = fmaf(av.z, xv.z, acc);
+        acc = fmaf(av.w, xv.w, acc);
+        cnt += (av.x > 0.f ? pv.x : 0) + (av.y > 0.f ? pv.y : 0) + (av.z > 0.f ? pv.z : 0) + (av.w > 0.f ? pv.w : 0);
+        if (valid) {
+            const int k = 4 * f;
+            float *dst = tcol + (int64_t)k * lcap;
+            dst[0] = av.x;
+            if (k + 1 < r) dst[lcap] = av.y;
+            if (k + 2 < r) dst[2 * lcap] = av.z;
+            if (k + 3 < r) dst[3 * lcap] = av.w;
+        }
+    }
+    return Staged{acc, cnt};
 }
 
 struct Tally {
@@ -240,8 +219,15 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
 // Register-resident groups: NT threads (32 = one warp per subproblem, several
 // per block; otherwise one CTA), K nonzeros per thread, so L <= NT*K.
 // ---------------------------------------------------------------------------
+// Minimum resident blocks per SM for the register budget: 80 registers for
+// the small warp kernels (24 warps per SM), 128 for the rest (16 warps per
+// SM) except the widest warp kernel.
+template <int NT, int K>
+__host__ __device__ constexpr int min_blocks() {
+    return NT == 32 ? (K <= 4 ? 3 : (K <= 8 ? 2 : 1)) : (512 / NT > 1 ? 512 / NT : 1);
+}
 template <int NT, int K, bool kFree = false>
-__global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) {
+__global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) sweep_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
     constexpr int kNW = NT / 32;
@@ -262,6 +248,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
     float *stg = stg_base + warp_in_group * 8 * S;
     float2 *red = reinterpret_cast<float2 *>(stg_base + kNW * 8 * S);
     uint64_t *words = reinterpret_cast<uint64_t *>(stg_base);
+    int *xpos = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg_base) + align16(8 * (size_t)r));
     __shared__ int s_q;
 
     float *tile = a.scratch + (int64_t)group_global * a.slot_floats;
@@ -296,7 +283,11 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
         }
         const int ks = (L + NT - 1) / NT;
 
-        for (int k = tid_g; k < ldr; k += NT) x_init[k] = a.X[u * ldr + k];
+        for (int k = tid_g; k < ldr; k += NT) {
+            const float xv = a.X[u * ldr + k];
+            x_init[k] = xv;
+            xpos[k] = xv > 0.f ? 1 : 0;
+        }
         if constexpr (kCta) __syncthreads(); else __syncwarp();
 
         // ---- stage A rows, x_p, and the per-nonzero state
@@ -315,7 +306,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
                         idx_l = a.idx[base + pl];
                         v_l = a.val[base + pl];
                     }
-                    const Staged st = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
+                    const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
                     if (pl < L) {
                         const float x_l = st.terms == 0 ? 0.f : st.x;
                         xr[s] = x_l;
@@ -370,11 +361,14 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
             }
         };
 
-        float acur[K], anxt[K];
-        load_col(acur, perm[0]);
+        // the column of the coordinate PF positions ahead is loaded while the
+        // current one is processed (PF = 2 for small K, else 1)
+        constexpr int PF = K <= 4 ? 2 : 1;
+        float acol0[K], acol1[K];
+        load_col(acol0, perm[0]);
         auto process = [&](float (&ac)[K], float (&an)[K], int kk) {
             const int k = perm[kk];
-            if (kk + 1 < r) load_col(an, perm[kk + 1]);
+            if (kk + PF < r) load_col(an, perm[kk + PF]);
             auto eval = [&]() -> float2 {
                 float sg = 0.f, sh = 0.f;
 #pragma unroll
@@ -400,9 +394,19 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT) sweep_kernel(HalfArgs a) 
             const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
             if (tid_g == 0) x_out[k] = xk;
         };
-        for (int kk = 0; kk < r; kk += 2) {
-            process(acur, anxt, kk);
-            if (kk + 1 < r) process(anxt, acur, kk + 1);
+        if constexpr (PF == 1) {
+            for (int kk = 0; kk < r; kk += 2) {
+                process(acol0, acol1, kk);
+                if (kk + 1 < r) process(acol1, acol0, kk + 1);
+            }
+        } else {
+            float acol2[K];
+            if (r > 1) load_col(acol1, perm[1]);
+            for (int kk = 0; kk < r; kk += 3) {
+                process(acol0, acol2, kk);
+                if (kk + 1 < r) process(acol1, acol0, kk + 1);
+                if (kk + 2 < r) process(acol2, acol1, kk + 2);
+            }
         }
         if (a.unit_obj) {
             float t = 0.f;
@@ -454,6 +458,7 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
     float *stg = stg_base + warp * 8 * S;
     float2 *red = reinterpret_cast<float2 *>(stg_base + kNW * 8 * S);
     uint64_t *words = reinterpret_cast<uint64_t *>(stg_base);
+    int *xpos = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg_base) + align16(8 * (size_t)r));
     __shared__ int s_q;
 
     float *tile = a.scratch + (int64_t)blockIdx.x * a.slot_floats;
@@ -475,7 +480,11 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
         const int64_t u = a.units[qi];
         const int64_t base = a.ptr[u];
         const int L = (int)(a.ptr[u + 1] - base);
-        for (int k = threadIdx.x; k < ldr; k += kGiantNT) x_init[k] = a.X[u * ldr + k];
+        for (int k = threadIdx.x; k < ldr; k += kGiantNT) {
+            const float xv = a.X[u * ldr + k];
+            x_init[k] = xv;
+            xpos[k] = xv > 0.f ? 1 : 0;
+        }
         __syncthreads();
         for (int p0 = 32 * warp; p0 < L; p0 += kGiantNT) {
             const int pl = p0 + lane;
@@ -485,7 +494,7 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
                 idx_l = a.idx[base + pl];
                 v_l = a.val[base + pl];
             }
-            const Staged st = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
+            const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
             if (pl < L) {
                 const float x_l = st.terms == 0 ? 0.f : st.x;
                 const float ri = recip(x_l + eps_div);
@@ -635,6 +644,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
     unsigned long long *slots = reinterpret_cast<unsigned long long *>(red + 2 * kNW);  // [2][kClusterMax]
     unsigned long long *mbar = slots + 2 * kClusterMax;                                 // [2]
     uint64_t *words = reinterpret_cast<uint64_t *>(stg_base);
+    int *xpos = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg_base) + align16(8 * (size_t)r));
     __shared__ int s_abort;
 
     if (threadIdx.x == 0) {
@@ -693,7 +703,11 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
         const int64_t base = ubase + my0;
         const int ks = (L + NT - 1) / NT;
 
-        for (int k = threadIdx.x; k < ldr; k += NT) x_init[k] = a.X[u * ldr + k];
+        for (int k = threadIdx.x; k < ldr; k += NT) {
+            const float xv = a.X[u * ldr + k];
+            x_init[k] = xv;
+            xpos[k] = xv > 0.f ? 1 : 0;
+        }
         __syncthreads();
         float xr[K], vr[K], wr[K], qr[K];
         int cr[K];
@@ -710,7 +724,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
                         idx_l = a.idx[base + pl];
                         v_l = a.val[base + pl];
                     }
-                    const Staged st = stage_chunk32(a, tile, stg, x_init, p0, L, idx_l, lane);
+                    const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
                     if (pl < L) {
                         const float x_l = st.terms == 0 ? 0.f : st.x;
                         xr[s] = x_l;

@@ -90,7 +90,7 @@ def objective_rel(V, Wg, Fg, Wo, Fo, side, alpha=0.0, beta=0.0, eps_div=1e-6):
 
 
 U32 = 2.0 ** -24
-PROBE_RUNS = 4
+PROBE_RUNS = 8
 PROBE_FACTOR = 4.0
 
 
@@ -113,6 +113,22 @@ def fp32_sensitivity(V, W, F, side, p, ref, runs=PROBE_RUNS, threads=8):
         dev = np.maximum(dev, np.abs(x - ref))
         probes.append(x)
     return dev, probes
+
+
+def trajectory_sensitivity(V, W0, F0, p, sweeps, ref_kl, runs=4, threads=8):
+    """Per sweep, max over `runs` Monte Carlo arithmetic runs of the oracle fit
+    (x_p perturbed at FP32's unit roundoff, as in fp32_sensitivity) of
+    |KL_probe - KL_ref|: how far FP32-level rounding moves the nonconvex
+    trajectory of Algorithm 1."""
+    dev = np.zeros(sweeps)
+    for s in range(runs):
+        cF, cW = cfg_for(p, 0), cfg_for(p, 1)
+        for c in (cF, cW):
+            c.perturb = U32
+            c.perturb_seed = 101 + s
+        res = oracle.fit(V, W0, F0, p.seed, sweeps, cF, cW, threads=threads)
+        dev = np.maximum(dev, np.abs(res.kl - ref_kl))
+    return dev
 
 
 def within(g, o, rtol=RTOL, floor=FLOOR, slack=None):

@@ -4,13 +4,15 @@ the same seeded inputs.
 Bars (FP32 path vs FP64 oracle), each half from an identical state:
   * tight mode (every coordinate solved to its 1-D minimiser): every entry
     within 1e-4 relative + 1e-6 x the unit's largest entry + 4 x its FP32
-    sensitivity (Monte Carlo arithmetic on the oracle, see fp32_sensitivity);
+    sensitivity (max over 8 Monte Carlo arithmetic runs of the oracle, see
+    fp32_sensitivity);
     the per-unit subproblem objective within 2e-6 of the magnitude of its
     terms (plus 4 x its probe spread);
   * the paper's constants (eps_x = 0.1): at least 99.5% of entries within the
     same bar (a break or clamp decision can flip between FP32 and FP64 for
     an entry on its threshold), per-unit objective within 1e-5, and the KL
-    trajectory over 20 sweeps within 1e-4 relative after every sweep;
+    trajectory over 20 sweeps within 1e-4 relative after every sweep, plus
+    4 x the spread FP32-level rounding gives the oracle's trajectory;
   * integer work (coordinate orders) and the random start: bit-exact.
 """
 import numpy as np
@@ -21,7 +23,7 @@ import paper_1604_04026_gb300 as nk
 from paper_1604_04026_gb300 import synth
 
 from _util import (PROBE_FACTOR, RTOL, TIGHT, cfg_for, designed_matrix, fp32_sensitivity, model,
-                   objective_scale, params, start, unit_objectives, within)
+                   objective_scale, params, start, trajectory_sensitivity, unit_objectives, within)
 
 pytestmark = pytest.mark.gpu
 
@@ -221,8 +223,11 @@ def test_kl_trajectory_20_sweeps(case, docs_small):
     traj, done = m.fit(20)
     assert done == 20
     ref = oracle.fit(V, W0, F0, 0, 20, cfg_for(p, 0), cfg_for(p, 1), threads=8)
-    rel = np.abs(traj - ref.kl) / ref.kl
-    assert rel.max() <= RTOL, rel
+    # the nonconvex path moves under FP32-level rounding; the bar adds that
+    # measured spread (it is far below 1e-4 on most sweeps)
+    spread = trajectory_sensitivity(V, W0, F0, p, 20, ref.kl)
+    err = np.abs(traj - ref.kl)
+    assert (err <= RTOL * ref.kl + PROBE_FACTOR * spread).all(), (err / ref.kl, spread / ref.kl)
     # monotone within FP32 noise
     assert (np.diff(traj) <= 1e-6 * traj[:-1]).all()
     m.close()
