@@ -42,6 +42,38 @@ __host__ __device__ inline size_t group_smem_bytes(int r, int ldr, int warps, bo
     return align16(b);
 }
 
+// Shared memory of a ring group (warp, CTA, or CTA of a cluster):
+//   perm (256 B) | x_init, x_out (ldr floats each) | Philox words, xpos flags |
+//   ring of D tile columns (per thread: K floats per slot) | CTA partials
+struct RingLayout {
+    size_t aux_off, xpos_off, ring_off, red_off, bytes;
+};
+__host__ __device__ inline RingLayout ring_layout(int r, int ldr, int nt, int k, int d, bool cta) {
+    RingLayout g{};
+    size_t off = align16(256 + 2 * (size_t)ldr * 4);
+    g.aux_off = off;
+    off = align16(off + 8 * (size_t)(r > 1 ? r - 1 : 1));
+    g.xpos_off = off;
+    off = align16(off + 4 * (size_t)ldr);
+    g.ring_off = off;
+    off = align16(off + (size_t)d * nt * k * 4);
+    g.red_off = off;
+    if (cta) off = align16(off + 2 * ((size_t)nt / 32) * sizeof(float2));
+    g.bytes = off;
+    return g;
+}
+
+// 4-byte global -> shared copy; src_bytes 0 writes a zero.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Fisher-Yates over {0..r-1} from the identity: step t (i = r-1-t) uses
 // word t, j = floor(word * (i+1) / 2^64).
 __device__ __forceinline__ void fisher_yates(uint8_t *perm, const uint64_t *words, int r) {
@@ -226,7 +258,7 @@ template <int NT, int K>
 __host__ __device__ constexpr int min_blocks() {
     return NT == 32 ? (K <= 4 ? 3 : (K <= 8 ? 2 : 1)) : (512 / NT > 1 ? 512 / NT : 1);
 }
-template <int NT, int K, bool kFree = false>
+template <int NT, int K, int D, bool kFree = false>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) sweep_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
@@ -240,15 +272,15 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
     const int group_global = blockIdx.x * groups_per_block + group_in_block;
 
     const int r = a.r, ldr = a.ldr, S = odd_stride(r);
-    unsigned char *gs = smem_raw + (size_t)group_in_block * group_smem_bytes(r, ldr, kNW, kCta);
+    const RingLayout lay = ring_layout(r, ldr, NT, K, D, kCta);
+    unsigned char *gs = smem_raw + (size_t)group_in_block * lay.bytes;
     uint8_t *perm = gs;
     float *x_init = reinterpret_cast<float *>(gs + 256);
     float *x_out = x_init + ldr;
-    float *stg_base = reinterpret_cast<float *>(gs + stage_offset(ldr));
-    float *stg = stg_base + warp_in_group * 8 * S;
-    float2 *red = reinterpret_cast<float2 *>(stg_base + kNW * 8 * S);
-    uint64_t *words = reinterpret_cast<uint64_t *>(stg_base);
-    int *xpos = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg_base) + align16(8 * (size_t)r));
+    uint64_t *words = reinterpret_cast<uint64_t *>(gs + lay.aux_off);
+    int *xpos = reinterpret_cast<int *>(gs + lay.xpos_off);
+    float *myring = reinterpret_cast<float *>(gs + lay.ring_off) + tid_g;  // slot d, item s at [(d*K + s)*NT]
+    float2 *red = reinterpret_cast<float2 *>(gs + lay.red_off);
     __shared__ int s_q;
 
     float *tile = a.scratch + (int64_t)group_global * a.slot_floats;
@@ -329,13 +361,18 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
         if constexpr (kCta) __syncthreads(); else __syncwarp();
 
         // ---- Algorithm 2 coordinate loop
-        auto load_col = [&](float (&dst)[K], int k) {
-            const float *col = tile + (int64_t)k * lcap;
+        // Each thread copies the tile entries it owns for the coordinate D-1
+        // positions ahead into its ring slots (cp.async; no other thread
+        // reads them), so the column is in shared memory when its turn comes.
+        auto issue = [&](int pos) {
+            if (pos < r) {
+                const float *col = tile + (int64_t)perm[pos] * lcap + tid_g;
+                float *dst = myring + (pos % D) * K * NT;
 #pragma unroll
-            for (int s = 0; s < K; ++s) {
-                const int p = tid_g + NT * s;
-                dst[s] = (s < ks && p < L) ? __ldcg(col + p) : 0.f;
+                for (int s = 0; s < K; ++s)
+                    if (s < ks) cp_async4(dst + s * NT, col + NT * s, tid_g + NT * s < L ? 4 : 0);
             }
+            cp_async_commit();
         };
         auto reduce = [&](float sg, float sh) -> float2 {
 #pragma unroll
@@ -360,22 +397,21 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                 return make_float2(sg, sh);
             }
         };
-
-        // the column of the coordinate PF positions ahead is loaded while the
-        // current one is processed (PF = 2 for small K, else 1)
-        constexpr int PF = K <= 4 ? 2 : 1;
-        float acol0[K], acol1[K];
-        load_col(acol0, perm[0]);
-        auto process = [&](float (&ac)[K], float (&an)[K], int kk) {
+#pragma unroll
+        for (int i = 0; i < D - 1; ++i) issue(i);
+        for (int kk = 0; kk < r; ++kk) {
+            issue(kk + D - 1);
+            cp_async_wait<D - 1>();
+            const float *ac = myring + (kk % D) * K * NT;
             const int k = perm[kk];
-            if (kk + PF < r) load_col(an, perm[kk + PF]);
             auto eval = [&]() -> float2 {
                 float sg = 0.f, sh = 0.f;
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
                     if (s < ks) {
-                        sg = fmaf(wr[s], ac[s], sg);
-                        sh = fmaf(qr[s] * ac[s], ac[s], sh);
+                        const float av = ac[s * NT];
+                        sg = fmaf(wr[s], av, sg);
+                        sh = fmaf(qr[s] * av, av, sh);
                     }
                 }
                 return reduce(sg, sh);
@@ -384,7 +420,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
                     if (s < ks) {
-                        xr[s] = step_x(xr[s], ac[s], d, dc, cr[s]);
+                        xr[s] = step_x(xr[s], ac[s * NT], d, dc, cr[s]);
                         const float ri = recip(xr[s] + eps_div);
                         wr[s] = vr[s] * ri;
                         qr[s] = wr[s] * ri;
@@ -393,21 +429,8 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
             };
             const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
             if (tid_g == 0) x_out[k] = xk;
-        };
-        if constexpr (PF == 1) {
-            for (int kk = 0; kk < r; kk += 2) {
-                process(acol0, acol1, kk);
-                if (kk + 1 < r) process(acol1, acol0, kk + 1);
-            }
-        } else {
-            float acol2[K];
-            if (r > 1) load_col(acol1, perm[1]);
-            for (int kk = 0; kk < r; kk += 3) {
-                process(acol0, acol2, kk);
-                if (kk + 1 < r) process(acol1, acol0, kk + 1);
-                if (kk + 2 < r) process(acol2, acol1, kk + 2);
-            }
         }
+        cp_async_wait<0>();
         if (a.unit_obj) {
             float t = 0.f;
 #pragma unroll
@@ -625,7 +648,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
     return done != 0;
 }
 
-template <int NT, int K>
+template <int NT, int K, int D>
 __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -635,16 +658,16 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
     constexpr int kNW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = a.r, ldr = a.ldr, S = odd_stride(r);
+    const RingLayout lay = ring_layout(r, ldr, NT, K, D, true);
     uint8_t *perm = smem_raw;
     float *x_init = reinterpret_cast<float *>(smem_raw + 256);
     float *x_out = x_init + ldr;
-    float *stg_base = reinterpret_cast<float *>(smem_raw + stage_offset(ldr));
-    float *stg = stg_base + warp * 8 * S;
-    float2 *red = reinterpret_cast<float2 *>(stg_base + kNW * 8 * S);
-    unsigned long long *slots = reinterpret_cast<unsigned long long *>(red + 2 * kNW);  // [2][kClusterMax]
-    unsigned long long *mbar = slots + 2 * kClusterMax;                                 // [2]
-    uint64_t *words = reinterpret_cast<uint64_t *>(stg_base);
-    int *xpos = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg_base) + align16(8 * (size_t)r));
+    uint64_t *words = reinterpret_cast<uint64_t *>(smem_raw + lay.aux_off);
+    int *xpos = reinterpret_cast<int *>(smem_raw + lay.xpos_off);
+    float *myring = reinterpret_cast<float *>(smem_raw + lay.ring_off) + threadIdx.x;
+    float2 *red = reinterpret_cast<float2 *>(smem_raw + lay.red_off);
+    unsigned long long *slots = reinterpret_cast<unsigned long long *>(smem_raw + lay.bytes);  // [2][kClusterMax]
+    unsigned long long *mbar = slots + 2 * kClusterMax;                                         // [2]
     __shared__ int s_abort;
 
     if (threadIdx.x == 0) {
@@ -745,13 +768,15 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
         }
         __syncthreads();
 
-        auto load_col = [&](float (&dst)[K], int k) {
-            const float *col = tile + (int64_t)k * lcap;
+        auto issue = [&](int pos) {
+            if (pos < r) {
+                const float *col = tile + (int64_t)perm[pos] * lcap + threadIdx.x;
+                float *dst = myring + (pos % D) * K * NT;
 #pragma unroll
-            for (int s = 0; s < K; ++s) {
-                const int p = threadIdx.x + NT * s;
-                dst[s] = (s < ks && p < L) ? __ldcg(col + p) : 0.f;
+                for (int s = 0; s < K; ++s)
+                    if (s < ks) cp_async4(dst + s * NT, col + NT * s, (int)threadIdx.x + NT * s < L ? 4 : 0);
             }
+            cp_async_commit();
         };
         auto reduce = [&](float sg, float sh) -> float2 {
 #pragma unroll
@@ -782,18 +807,21 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
             return tot;
         };
 
-        float acur[K], anxt[K];
-        load_col(acur, perm[0]);
-        auto process = [&](float (&ac)[K], float (&an)[K], int kk) {
+#pragma unroll
+        for (int i = 0; i < D - 1; ++i) issue(i);
+        for (int kk = 0; kk < r; ++kk) {
+            issue(kk + D - 1);
+            cp_async_wait<D - 1>();
+            const float *ac = myring + (kk % D) * K * NT;
             const int k = perm[kk];
-            if (kk + 1 < r) load_col(an, perm[kk + 1]);
             auto eval = [&]() -> float2 {
                 float sg = 0.f, sh = 0.f;
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
                     if (s < ks) {
-                        sg = fmaf(wr[s], ac[s], sg);
-                        sh = fmaf(qr[s] * ac[s], ac[s], sh);
+                        const float av = ac[s * NT];
+                        sg = fmaf(wr[s], av, sg);
+                        sh = fmaf(qr[s] * av, av, sh);
                     }
                 }
                 return reduce(sg, sh);
@@ -802,7 +830,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
                     if (s < ks) {
-                        xr[s] = step_x(xr[s], ac[s], d, dc, cr[s]);
+                        xr[s] = step_x(xr[s], ac[s * NT], d, dc, cr[s]);
                         const float ri = recip(xr[s] + eps_div);
                         wr[s] = vr[s] * ri;
                         qr[s] = wr[s] * ri;
@@ -811,11 +839,8 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
             };
             const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
             if (threadIdx.x == 0) x_out[k] = xk;
-        };
-        for (int kk = 0; kk < r; kk += 2) {
-            process(acur, anxt, kk);
-            if (kk + 1 < r) process(anxt, acur, kk + 1);
         }
+        cp_async_wait<0>();
         if (a.unit_obj) {
             float t = 0.f;
 #pragma unroll
@@ -855,25 +880,26 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 struct KernelKind {
     const void *fn;
     int nt, k, cl;  // threads per CTA (32: warp groups), nonzeros per thread, CTAs per cluster
+    int d;          // ring depth (tile columns in flight); 0 for the giant kernel
     const char *name;
 };
 
-constexpr int kClusterNT = 512, kClusterK = 12;
+constexpr int kClusterNT = 512, kClusterK = 12, kClusterD = 4;
 const KernelKind kKinds[] = {
-    {(const void *)sweep_kernel<32, 1>, 32, 1, 1, "sweep_warp_k1"},
-    {(const void *)sweep_kernel<32, 2>, 32, 2, 1, "sweep_warp_k2"},
-    {(const void *)sweep_kernel<32, 4>, 32, 4, 1, "sweep_warp_k4"},
-    {(const void *)sweep_kernel<32, 8>, 32, 8, 1, "sweep_warp_k8"},
-    {(const void *)sweep_kernel<32, 16>, 32, 16, 1, "sweep_warp_k16"},
-    {(const void *)sweep_kernel<128, 8>, 128, 8, 1, "sweep_cta128_k8"},
-    {(const void *)sweep_kernel<256, 8>, 256, 8, 1, "sweep_cta256_k8"},
-    {(const void *)sweep_kernel<512, 8>, 512, 8, 1, "sweep_cta512_k8"},
-    {(const void *)sweep_kernel<512, 16>, 512, 16, 1, "sweep_cta512_k16"},
-    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK>, kClusterNT, kClusterK, 2, "sweep_cluster2"},
-    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK>, kClusterNT, kClusterK, 4, "sweep_cluster4"},
-    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK>, kClusterNT, kClusterK, 8, "sweep_cluster8"},
-    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK>, kClusterNT, kClusterK, 16, "sweep_cluster16"},
-    {(const void *)sweep_giant_kernel, kGiantNT, 0, 1, "sweep_giant"},
+    {(const void *)sweep_kernel<32, 1, 8>, 32, 1, 1, 8, "sweep_warp_k1"},
+    {(const void *)sweep_kernel<32, 2, 8>, 32, 2, 1, 8, "sweep_warp_k2"},
+    {(const void *)sweep_kernel<32, 4, 8>, 32, 4, 1, 8, "sweep_warp_k4"},
+    {(const void *)sweep_kernel<32, 8, 6>, 32, 8, 1, 6, "sweep_warp_k8"},
+    {(const void *)sweep_kernel<32, 16, 4>, 32, 16, 1, 4, "sweep_warp_k16"},
+    {(const void *)sweep_kernel<128, 8, 8>, 128, 8, 1, 8, "sweep_cta128_k8"},
+    {(const void *)sweep_kernel<256, 8, 6>, 256, 8, 1, 6, "sweep_cta256_k8"},
+    {(const void *)sweep_kernel<512, 8, 4>, 512, 8, 1, 4, "sweep_cta512_k8"},
+    {(const void *)sweep_kernel<512, 16, 3>, 512, 16, 1, 3, "sweep_cta512_k16"},
+    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK, kClusterD>, kClusterNT, kClusterK, 2, kClusterD, "sweep_cluster2"},
+    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK, kClusterD>, kClusterNT, kClusterK, 4, kClusterD, "sweep_cluster4"},
+    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK, kClusterD>, kClusterNT, kClusterK, 8, kClusterD, "sweep_cluster8"},
+    {(const void *)sweep_cluster_kernel<kClusterNT, kClusterK, kClusterD>, kClusterNT, kClusterK, 16, kClusterD, "sweep_cluster16"},
+    {(const void *)sweep_giant_kernel, kGiantNT, 0, 1, 0, "sweep_giant"},
 };
 constexpr int kNumKinds = sizeof(kKinds) / sizeof(kKinds[0]);
 constexpr int kGiantKind = kNumKinds - 1;
@@ -886,7 +912,8 @@ int kind_for_length(int64_t L, const std::vector<char> &usable) {
 }
 
 size_t cluster_smem_bytes(int r, int ldr) {
-    return group_smem_bytes(r, ldr, kClusterNT / 32, true) + (2 * kClusterMax + 2) * sizeof(unsigned long long);
+    return ring_layout(r, ldr, kClusterNT, kClusterK, kClusterD, true).bytes +
+           (2 * kClusterMax + 2) * sizeof(unsigned long long);
 }
 
 // Clusters of `cl` CTAs of the cluster kernel that fit on the device at once.
@@ -986,7 +1013,8 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
         }
         const bool cta = b.nt > 32;
         const int warps = b.nt / 32;
-        const size_t gbytes = group_smem_bytes(r, ldr, cta ? warps : 1, cta);
+        const size_t gbytes = kind == kGiantKind ? group_smem_bytes(r, ldr, warps, true)
+                                                 : ring_layout(r, ldr, b.nt, b.k, kKinds[kind].d, cta).bytes;
         int groups_per_block = 1;
         if (!cta) {
             groups_per_block = 8;
@@ -1131,10 +1159,10 @@ struct NoAllocCtl {  // lives at the start of the control block
 };
 
 const KernelKind kFreeKinds[] = {
-    {(const void *)sweep_kernel<32, 1, true>, 32, 1, 1, "sweep_warp_k1_noalloc"},
-    {(const void *)sweep_kernel<32, 2, true>, 32, 2, 1, "sweep_warp_k2_noalloc"},
-    {(const void *)sweep_kernel<32, 4, true>, 32, 4, 1, "sweep_warp_k4_noalloc"},
-    {(const void *)sweep_kernel<32, 8, true>, 32, 8, 1, "sweep_warp_k8_noalloc"},
+    {(const void *)sweep_kernel<32, 1, 8, true>, 32, 1, 1, 8, "sweep_warp_k1_noalloc"},
+    {(const void *)sweep_kernel<32, 2, 8, true>, 32, 2, 1, 8, "sweep_warp_k2_noalloc"},
+    {(const void *)sweep_kernel<32, 4, 8, true>, 32, 4, 1, 8, "sweep_warp_k4_noalloc"},
+    {(const void *)sweep_kernel<32, 8, 6, true>, 32, 8, 1, 6, "sweep_warp_k8_noalloc"},
 };
 }  // namespace
 
@@ -1178,7 +1206,7 @@ extern "C" nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, 
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     optin -= 1024;
-    const size_t gbytes = group_smem_bytes(r, ldr, 1, false);
+    const size_t gbytes = ring_layout(r, ldr, 32, kk.k, kk.d, false).bytes;
     int gpb = 8;
     while (gpb > 1 && gbytes * gpb > (size_t)optin) --gpb;
     const size_t smem = gbytes * gpb;
