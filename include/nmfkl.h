@@ -155,6 +155,42 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *ctx, int64_t sweep0, int32_t max_sweeps, doubl
  * Synchronizes (the objective is read back). */
 nmfkl_status nmfkl_step(nmfkl_ctx *ctx, int64_t sweep, double *kl);
 
+/* Fold-in: F for m_new new documents (columns of a new V', n x m_new)
+ * under the context's current W, held fixed -- Algorithm 1's F half alone
+ * (Section 2: each column is the independent subproblem of Eq. 3 with
+ * A = W^T, sumA = sumW, alpha = a2, beta = b2), repeated per column until
+ * its objective settles.
+ *
+ * Column j starts from F0[:, j] and runs passes s = 0, 1, ... of Algorithm 2
+ * with the order ids(seed, sweep s, side 0, unit u_j), u_j = doc_ids[j] if
+ * doc_ids is given, else j. Before the first pass and after every pass its
+ * objective
+ *   D_j = sum_{p in nnz(j)} [v_p log(v_p / (x_p + eps_div)) - v_p]
+ *         + sum_k (sumW_k F_kj + a2/2 F_kj^2 + b2 |F_kj|)
+ * is evaluated (FP32 terms at the model values of the pass, FP64 sums); the
+ * column stops after the first pass with |D_prev - D| <= rel_tol * |D_prev|,
+ * or after max_sweeps passes. A column is never affected by the others: its
+ * result is the same whatever batch it is submitted in.
+ *
+ * Inputs (host or device per mem_kind): colptr int64[m_new+1], rowidx
+ * int32[nnz] (< n, strictly increasing per column), val float[nnz] (finite,
+ * > 0); at most 8192 nonzeros per column (EINVAL beyond). doc_ids int64[m_new]
+ * or NULL. F0 float[r * m_new] row-major, or NULL to draw it from
+ * Uniform[0,1) as nmfkl_init does with which = 2.
+ * Outputs: F_out float[r * m_new] row-major; sweeps_done int32[m_new] and
+ * doc_obj double[m_new] (D_j at the returned column), each may be NULL.
+ *
+ * launch_mode 0: one persistent launch per length class, the whole sequence
+ * captured once into a CUDA graph and replayed while m_new, doc_ids given or
+ * not, rel_tol and max_sweeps stay the same; 1: the same launches without
+ * the graph; 2: one launch per column (the plain scheme, for comparison).
+ * Synchronizes. Device memory for the inputs and the tiles is kept in the
+ * context and reused. */
+nmfkl_status nmfkl_foldin(nmfkl_ctx *ctx, int64_t m_new, int64_t nnz, const int64_t *colptr,
+                          const int32_t *rowidx, const float *val, const int64_t *doc_ids,
+                          const float *F0, float *F_out, double rel_tol, int32_t max_sweeps,
+                          int32_t *sweeps_done, double *doc_obj, int32_t launch_mode, int32_t mem_kind);
+
 /* Copies W (r x n) or F (r x m), row-major FP32, to host or device memory. */
 nmfkl_status nmfkl_get_W(nmfkl_ctx *ctx, float *out, int32_t mem_kind);
 nmfkl_status nmfkl_get_F(nmfkl_ctx *ctx, float *out, int32_t mem_kind);

@@ -165,6 +165,41 @@ class NMFKL:
         self._check(self._lib.nmfkl_step(self._h, int(sweep), ctypes.byref(kl)), "step")
         return kl.value
 
+    def foldin(self, V=None, *, colptr=None, rowidx=None, val=None, nnz=None, doc_ids=None, F0=None,
+               rel_tol: float = 1e-5, max_sweeps: int = 100, launch_mode: int = 0, out=None):
+        """F (r x m_new) for new documents under the current W (held fixed).
+
+        V: a synth.CountMatrix with n rows (host), or colptr/rowidx/val as numpy
+        arrays or CUDA tensors. Returns (F, sweeps per document, objective per
+        document); with CUDA inputs the three results are CUDA tensors."""
+        if V is not None:
+            colptr, rowidx, val, nnz = V.colptr, V.rowidx, V.val, V.nnz
+        p = [_ptr(colptr, np.int64), _ptr(rowidx, np.int32), _ptr(val, np.float32), _ptr(doc_ids, np.int64),
+             _ptr(F0, np.float32)]
+        kinds = {k for x, k, _ in p if x is not None}
+        if len(kinds) > 1:
+            raise ValueError("mix of host and device arrays")
+        kind = kinds.pop() if kinds else 0
+        m_new = int(colptr.shape[0]) - 1
+        if nnz is None:
+            nnz = int(rowidx.shape[0])
+        if kind == 1:
+            import torch
+            dev = colptr.device
+            F = out if out is not None else torch.empty((self.r, m_new), dtype=torch.float32, device=dev)
+            sweeps = torch.empty(max(m_new, 1), dtype=torch.int32, device=dev)
+            obj = torch.empty(max(m_new, 1), dtype=torch.float64, device=dev)
+            pf, ps, po = F.data_ptr(), sweeps.data_ptr(), obj.data_ptr()
+        else:
+            F = out if out is not None else np.empty((self.r, m_new), dtype=np.float32)
+            sweeps = np.zeros(max(m_new, 1), dtype=np.int32)
+            obj = np.zeros(max(m_new, 1), dtype=np.float64)
+            pf, ps, po = F.ctypes.data, sweeps.ctypes.data, obj.ctypes.data
+        st = self._lib.nmfkl_foldin(self._h, m_new, int(nnz), p[0][0], p[1][0], p[2][0], p[3][0], p[4][0], pf,
+                                    float(rel_tol), int(max_sweeps), ps, po, int(launch_mode), kind)
+        self._check(st, "foldin")
+        return F, sweeps[:m_new], obj[:m_new]
+
     def plan(self) -> list:
         """Launch plan: one dict per (half, length bucket)."""
         cap = 64

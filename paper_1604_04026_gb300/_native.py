@@ -47,6 +47,8 @@ SIGNATURES = [
     ("nmfkl_fit", c_i32, [c_vp, c_i64, c_i32, c_f64, c_vp, ctypes.POINTER(c_i32)]),
     ("nmfkl_step", c_i32, [c_vp, c_i64, ctypes.POINTER(c_f64)]),
     ("nmfkl_plan_info", c_i32, [c_vp, c_vp, c_i32]),
+    ("nmfkl_foldin", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_f64, c_i32, c_vp, c_vp,
+                             c_i32, c_i32]),
     ("nmfkl_get_W", c_i32, [c_vp, c_vp, c_i32]),
     ("nmfkl_get_F", c_i32, [c_vp, c_vp, c_i32]),
     ("nmfkl_get_counters", c_i32, [c_vp, ctypes.POINTER(Counters), c_i32]),

@@ -199,6 +199,7 @@ void nmfkl_destroy(nmfkl_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     free_data(c);
+    free_fold(c);
     cudaFree(c->Wt); cudaFree(c->Ft); cudaFree(c->sumW); cudaFree(c->sumF); cudaFree(c->dpart);
     cudaFree(c->dscalar); cudaFree(c->counters); cudaFree(c->queues); cudaFree(c->err_flag);
     cudaFree(c->tbuf);
@@ -423,6 +424,141 @@ nmfkl_status nmfkl_step(nmfkl_ctx *c, int64_t sweep, double *kl) {
     if (st == NMFKL_OK) st = run_half(c, 1, sweep);
     if (st == NMFKL_OK) st = launch_fused_objective(c, kl);
     return st;
+}
+
+// Grows the fold-in input buffers to hold m_new columns and nnz nonzeros.
+static nmfkl_status fold_reserve(nmfkl_ctx *c, int64_t m_new, int64_t nnz) {
+    if (!c->fold) {
+        c->fold = new (std::nothrow) FoldState();
+        if (!c->fold) return NMFKL_ENOMEM;
+    }
+    FoldState &f = *c->fold;
+    if (m_new > f.cap_m) {
+        const int64_t cap = std::max<int64_t>(m_new, 2 * f.cap_m);
+        cudaFree(f.colptr); cudaFree(f.ids); cudaFree(f.Ft); cudaFree(f.Fout); cudaFree(f.lists);
+        cudaFree(f.sweeps); cudaFree(f.obj);
+        f.colptr = f.ids = nullptr;
+        f.Ft = f.Fout = nullptr;
+        f.lists = f.sweeps = nullptr;
+        f.obj = nullptr;
+        f.cap_m = 0;
+        if (!(dev_alloc(c, &f.colptr, cap + 1, "fold-in colptr") && dev_alloc(c, &f.ids, cap, "fold-in ids") &&
+              dev_alloc(c, &f.Ft, cap * c->ldr, "fold-in F") && dev_alloc(c, &f.Fout, cap * c->p.r, "fold-in out") &&
+              dev_alloc(c, &f.lists, cap * kFoldKinds, "fold-in lists") &&
+              dev_alloc(c, &f.sweeps, cap, "fold-in sweeps") && dev_alloc(c, &f.obj, cap, "fold-in objective")))
+            return NMFKL_ENOMEM;
+        if (!cuda_ok(c, cudaMemset(f.Ft, 0, sizeof(float) * cap * c->ldr), "zero fold-in F")) return NMFKL_ECUDA;
+        f.cap_m = cap;
+        if (f.graph) {
+            cudaGraphExecDestroy(f.graph);
+            f.graph = nullptr;
+        }
+    }
+    if (!f.ctl && !dev_alloc(c, &f.ctl, 2 * kFoldKinds + 1, "fold-in control")) return NMFKL_ENOMEM;
+    if (nnz > f.cap_nnz) {
+        const int64_t cap = std::max<int64_t>(nnz, 2 * f.cap_nnz);
+        cudaFree(f.rowidx); cudaFree(f.val);
+        f.rowidx = nullptr;
+        f.val = nullptr;
+        f.cap_nnz = 0;
+        if (!(dev_alloc(c, &f.rowidx, cap, "fold-in rowidx") && dev_alloc(c, &f.val, cap, "fold-in val")))
+            return NMFKL_ENOMEM;
+        f.cap_nnz = cap;
+        if (f.graph) {
+            cudaGraphExecDestroy(f.graph);
+            f.graph = nullptr;
+        }
+    }
+    return NMFKL_OK;
+}
+
+nmfkl_status nmfkl_foldin(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_t *colptr, const int32_t *rowidx,
+                          const float *val, const int64_t *doc_ids, const float *F0, float *F_out, double rel_tol,
+                          int32_t max_sweeps, int32_t *sweeps_done, double *doc_obj, int32_t launch_mode,
+                          int32_t mem_kind) {
+    if (!c) return NMFKL_EINVAL;
+    if (m_new < 0 || m_new > INT32_MAX || nnz < 0 || !colptr || (nnz > 0 && (!rowidx || !val)) || !F_out ||
+        !(rel_tol >= 0) || max_sweeps < 0 || launch_mode < 0 || launch_mode > 2 || (mem_kind != 0 && mem_kind != 1)) {
+        c->err = "foldin: bad arguments";
+        return NMFKL_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    const int64_t r = c->p.r;
+    if (mem_kind == 0) {
+        if (!check_host(c, m_new, c->n, nnz, colptr, rowidx, val, "fold-in CSC")) return NMFKL_EINVAL;
+        for (int64_t j = 0; j < m_new; ++j)
+            if (foldin_kind_for_length(colptr[j + 1] - colptr[j]) < 0) {
+                c->err = "foldin: a column has more than 8192 nonzeros";
+                return NMFKL_EINVAL;
+            }
+    }
+    nmfkl_status st = fold_reserve(c, m_new, nnz);
+    if (st != NMFKL_OK) return st;
+    FoldState &f = *c->fold;
+    const cudaMemcpyKind in_kind = mem_kind == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind out_kind = mem_kind == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    bool ok = cuda_ok(c, cudaMemcpyAsync(f.colptr, colptr, 8 * (m_new + 1), in_kind, c->stream), "copy fold-in colptr");
+    if (ok && nnz > 0)
+        ok = cuda_ok(c, cudaMemcpyAsync(f.rowidx, rowidx, 4 * nnz, in_kind, c->stream), "copy fold-in rowidx") &&
+             cuda_ok(c, cudaMemcpyAsync(f.val, val, 4 * nnz, in_kind, c->stream), "copy fold-in val");
+    if (ok && doc_ids && m_new > 0)
+        ok = cuda_ok(c, cudaMemcpyAsync(f.ids, doc_ids, 8 * m_new, in_kind, c->stream), "copy fold-in ids");
+    if (!ok) return NMFKL_ECUDA;
+    if (mem_kind == 1) {
+        int32_t h = 0;
+        int64_t last = 0;
+        ok = cuda_ok(c, cudaMemsetAsync(c->err_flag, 0, 4, c->stream), "flag") &&
+             launch_validate(c, m_new, c->n, f.colptr, f.rowidx, f.val, c->err_flag) == NMFKL_OK &&
+             cuda_ok(c, cudaMemcpyAsync(&h, c->err_flag, 4, cudaMemcpyDeviceToHost, c->stream), "flag copy") &&
+             cuda_ok(c, cudaMemcpyAsync(&last, f.colptr + m_new, 8, cudaMemcpyDeviceToHost, c->stream), "nnz copy") &&
+             cuda_ok(c, cudaStreamSynchronize(c->stream), "validate sync") &&
+             cuda_ok(c, cudaMemsetAsync(c->err_flag, 0, 4, c->stream), "flag");
+        if (!ok) return NMFKL_ECUDA;
+        if (h != 0 || last != nnz) {
+            c->err = "foldin: device input failed validation (offsets, sorted in-range indices, values > 0)";
+            return NMFKL_EINVAL;
+        }
+    }
+    // starting F, unit-major
+    if (m_new > 0) {
+        if (!F0) {
+            uniform_init_raw(c->stream, f.Ft, c->p.r, m_new, c->ldr, c->p.seed, 2);
+        } else {
+            if (c->tbuf_floats < r * m_new) {
+                cudaFree(c->tbuf);
+                c->tbuf = nullptr;
+                c->tbuf_floats = 0;
+                if (!dev_alloc(c, &c->tbuf, r * m_new, "transpose buffer")) return NMFKL_ENOMEM;
+                c->tbuf_floats = r * m_new;
+            }
+            if (!cuda_ok(c, cudaMemcpyAsync(c->tbuf, F0, sizeof(float) * r * m_new, in_kind, c->stream), "copy F0"))
+                return NMFKL_ECUDA;
+            st = launch_to_unit_major(c, c->tbuf, f.Ft, m_new);
+            if (st != NMFKL_OK) return st;
+        }
+    }
+    st = launch_mode == 2 ? foldin_per_doc(c, m_new, rel_tol, max_sweeps)
+                          : foldin_run(c, m_new, doc_ids != nullptr, rel_tol, max_sweeps, launch_mode == 0);
+    if (st != NMFKL_OK) return st;
+    int32_t err = 0;
+    ok = cuda_ok(c, cudaMemcpyAsync(&err, f.ctl + 2 * kFoldKinds, 4, cudaMemcpyDeviceToHost, c->stream), "fold-in flags");
+    if (ok && m_new > 0) {
+        ok = cuda_ok(c, cudaMemcpyAsync(F_out, f.Fout, sizeof(float) * r * m_new, out_kind, c->stream), "copy F_out");
+        if (ok && sweeps_done)
+            ok = cuda_ok(c, cudaMemcpyAsync(sweeps_done, f.sweeps, 4 * m_new, out_kind, c->stream), "copy sweeps");
+        if (ok && doc_obj)
+            ok = cuda_ok(c, cudaMemcpyAsync(doc_obj, f.obj, 8 * m_new, out_kind, c->stream), "copy objectives");
+    }
+    if (!ok || !cuda_ok(c, cudaStreamSynchronize(c->stream), "fold-in sync")) return NMFKL_ECUDA;
+    if (err & 4) {
+        c->err = "foldin: a column has more than 8192 nonzeros";
+        return NMFKL_EINVAL;
+    }
+    if (err & 1) {
+        c->err = "foldin: NaN produced";
+        return NMFKL_ENUMERIC;
+    }
+    return NMFKL_OK;
 }
 
 int32_t nmfkl_plan_info(const nmfkl_ctx *c, nmfkl_bucket_info *out, int32_t cap) {

@@ -305,6 +305,10 @@ nmfkl_status launch_uniform_init(nmfkl_ctx *c, int which, float *X, int64_t cols
     return cuda_ok(c, cudaGetLastError(), "uniform_init") ? NMFKL_OK : NMFKL_ECUDA;
 }
 
+void uniform_init_raw(cudaStream_t st, float *X, int r, int64_t cols, int ldr, uint64_t seed, int which) {
+    uniform_init_kernel<<<1024, 256, 0, st>>>(X, r, cols, ldr, seed, which);
+}
+
 nmfkl_status launch_to_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols) {
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((c->ldr + 31) / 32));
     const int tok = timer_begin(c, "transpose");
@@ -319,6 +323,11 @@ nmfkl_status launch_from_unit_major(nmfkl_ctx *c, const float *src, float *dst, 
     from_unit_major_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(src, dst, c->p.r, cols, c->ldr);
     timer_end(c, tok);
     return cuda_ok(c, cudaGetLastError(), "from_unit_major") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+void launch_from_unit_major_raw(cudaStream_t st, const float *src, float *dst, int r, int64_t cols, int ldr) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((r + 31) / 32));
+    from_unit_major_kernel<<<grid, dim3(32, 8), 0, st>>>(src, dst, r, cols, ldr);
 }
 
 nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, const int64_t *ptr,

@@ -81,6 +81,14 @@ struct HalfArgs {
     int32_t *err;          // device error flag
     double *unit_obj;      // if set: per unit, sum over its nonzeros of v log(v/(x+eps)) - v
                            // at the unit's final x (Eq. 1's data term, fused into the W half)
+    const int32_t *count_dev;  // if set, the bucket's unit count is read here (device-built buckets)
+    const int64_t *unit_ids;   // if set, the unit id that keys the coordinate order (else the unit index)
+    // fold-in (F half alone under a fixed W, every column to its own stopping point)
+    int32_t max_sweeps;
+    double rel_tol;
+    const double *sumA64;  // FP64 column sums of the fixed factor (the objective's linear term)
+    int32_t *sweeps_done;  // per unit
+    double *unit_final;    // per unit: the column objective at the returned x
 };
 
 // One launch configuration of the sweep kernel family.
@@ -99,6 +107,35 @@ struct Bucket {
     int64_t slot_floats;
     int64_t max_len;
     int64_t nnz;      // nonzeros of the bucket's units
+};
+
+// Device state of fold-in (nmfkl_foldin): input copies, per-length-class
+// unit lists built on the device, tiles, and the captured launch graph.
+constexpr int kFoldKinds = 9;
+struct FoldState {
+    int64_t cap_m = 0, cap_nnz = 0;
+    int64_t *colptr = nullptr, *ids = nullptr;
+    int32_t *rowidx = nullptr;
+    float *val = nullptr;
+    float *Ft = nullptr;       // cap_m x ldr, unit-major
+    float *Fout = nullptr;     // r x cap_m, row-major
+    int32_t *lists = nullptr;  // kFoldKinds x cap_m
+    int32_t *ctl = nullptr;    // [counts kFoldKinds][queues kFoldKinds][err]
+    int32_t *sweeps = nullptr;
+    double *obj = nullptr;
+    float *scratch = nullptr;
+    int64_t scratch_floats = 0;
+    bool planned = false;
+    int grid[kFoldKinds] = {}, block[kFoldKinds] = {}, groups[kFoldKinds] = {};
+    size_t smem[kFoldKinds] = {};
+    int64_t slot_floats[kFoldKinds] = {};
+    int32_t lcap[kFoldKinds] = {};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_m = -1;
+    bool graph_ids = false;
+    double graph_tol = -1.0;
+    int32_t graph_sweeps = -1;
 };
 
 struct KernelTimer {
@@ -138,6 +175,7 @@ struct nmfkl_ctx {
     float *tbuf = nullptr;         // transpose staging for get/set
     int64_t tbuf_floats = 0;
     std::vector<nmfkl::Bucket> plan[2];
+    nmfkl::FoldState *fold = nullptr;
     // timing
     bool timing = false;
     std::vector<nmfkl::KernelTimer> timers;
@@ -171,9 +209,17 @@ nmfkl_status launch_objective(nmfkl_ctx *c, double *kl, double *reg);
 nmfkl_status launch_uniform_init(nmfkl_ctx *c, int which, float *X, int64_t cols);
 nmfkl_status launch_to_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols);
 nmfkl_status launch_from_unit_major(nmfkl_ctx *c, const float *src, float *dst, int64_t cols);
+void uniform_init_raw(cudaStream_t st, float *X, int r, int64_t cols, int ldr, uint64_t seed, int which);
+void launch_from_unit_major_raw(cudaStream_t st, const float *src, float *dst, int r, int64_t cols, int ldr);
 nmfkl_status launch_debug_perm(nmfkl_ctx *c, int64_t sweep, int side, int64_t count,
                                const int64_t *cols, int32_t *out);
 int64_t dpart_required(int ldr);
+// sweep.cu: fold-in
+nmfkl_status foldin_run(nmfkl_ctx *c, int64_t m_new, bool with_ids, double rel_tol, int32_t max_sweeps,
+                        bool use_graph);
+nmfkl_status foldin_per_doc(nmfkl_ctx *c, int64_t m_new, double rel_tol, int32_t max_sweeps);
+int foldin_kind_for_length(int64_t L);
+void free_fold(nmfkl_ctx *c);
 nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, const int64_t *ptr,
                              const int32_t *idx, const float *val, int32_t *flag);
 

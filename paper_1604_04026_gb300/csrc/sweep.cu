@@ -144,22 +144,36 @@ __device__ __forceinline__ Staged stage_lane(const HalfArgs &a, float *tile, con
     float *tcol = tile + p;
     float acc = 0.f;
     int cnt = 0;
-    for (int f = 0; f < nf4; ++f) {
-        const float4 av = valid ? __ldg(row + f) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 xv = x4[f];
-        const int4 pv = p4[f];
-        acc = fmaf(av.x, xv.x, acc);
-        acc = fmaf(av.y, xv.y, acc);
-        acc = fmaf(av.z, xv.z, acc);
-        acc = fmaf(av.w, xv.w, acc);
-        cnt += (av.x > 0.f ? pv.x : 0) + (av.y > 0.f ? pv.y : 0) + (av.z > 0.f ? pv.z : 0) + (av.w > 0.f ? pv.w : 0);
-        if (valid) {
-            const int k = 4 * f;
-            float *dst = tcol + (int64_t)k * lcap;
-            dst[0] = av.x;
-            if (k + 1 < r) dst[lcap] = av.y;
-            if (k + 2 < r) dst[2 * lcap] = av.z;
-            if (k + 3 < r) dst[3 * lcap] = av.w;
+    // The row is read kStageBatch 16-byte pieces at a time, all issued before
+    // the first is used, so that many gathers are in flight per lane.
+    constexpr int kStageBatch = 8;
+    for (int f0 = 0; f0 < nf4; f0 += kStageBatch) {
+        float4 buf[kStageBatch];
+#pragma unroll
+        for (int b = 0; b < kStageBatch; ++b)
+            buf[b] = (valid && f0 + b < nf4) ? __ldg(row + f0 + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < kStageBatch; ++b) {
+            const int f = f0 + b;
+            if (f < nf4) {
+                const float4 av = buf[b];
+                const float4 xv = x4[f];
+                const int4 pv = p4[f];
+                acc = fmaf(av.x, xv.x, acc);
+                acc = fmaf(av.y, xv.y, acc);
+                acc = fmaf(av.z, xv.z, acc);
+                acc = fmaf(av.w, xv.w, acc);
+                cnt += (av.x > 0.f ? pv.x : 0) + (av.y > 0.f ? pv.y : 0) + (av.z > 0.f ? pv.z : 0) +
+                       (av.w > 0.f ? pv.w : 0);
+                if (valid) {
+                    const int k = 4 * f;
+                    float *dst = tcol + (int64_t)k * lcap;
+                    dst[0] = av.x;
+                    if (k + 1 < r) dst[lcap] = av.y;
+                    if (k + 2 < r) dst[2 * lcap] = av.z;
+                    if (k + 3 < r) dst[3 * lcap] = av.w;
+                }
+            }
         }
     }
     return Staged{acc, cnt};
@@ -258,7 +272,12 @@ template <int NT, int K>
 __host__ __device__ constexpr int min_blocks() {
     return NT == 32 ? (K <= 4 ? 3 : (K <= 8 ? 2 : 1)) : (512 / NT > 1 ? 512 / NT : 1);
 }
-template <int NT, int K, int D, bool kFree = false>
+// Kernel modes: one half sweep, the allocation-free F half (units are the
+// column indices themselves), and fold-in (each column runs its own sweeps of
+// Algorithm 2 until its objective settles, with the tile staged once).
+constexpr int kModeHalf = 0, kModeFree = 1, kModeFold = 2;
+
+template <int NT, int K, int D, int kMode = kModeHalf>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) sweep_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
@@ -271,7 +290,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
     const int tid_g = kCta ? (int)threadIdx.x : lane;
     const int group_global = blockIdx.x * groups_per_block + group_in_block;
 
-    const int r = a.r, ldr = a.ldr, S = odd_stride(r);
+    const int r = a.r, ldr = a.ldr;
     const RingLayout lay = ring_layout(r, ldr, NT, K, D, kCta);
     unsigned char *gs = smem_raw + (size_t)group_in_block * lay.bytes;
     uint8_t *perm = gs;
@@ -286,8 +305,29 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
     float *tile = a.scratch + (int64_t)group_global * a.slot_floats;
     const int lcap = a.lcap;
     const float eps_div = a.eps_div;
+    const int count = a.count_dev ? *a.count_dev : a.count;
     Tally tally;
     int parity = 0;
+
+    auto group_sync = [&]() {
+        if constexpr (kCta) __syncthreads(); else __syncwarp();
+    };
+    // Sum of one double per thread over the group, identical in every thread.
+    auto group_sum_d = [&](double t) -> double {
+        t = warp_sum_d(t);
+        if constexpr (kCta) {
+            double *rd = reinterpret_cast<double *>(red + parity * kNW);
+            if (lane == 0) rd[warp_in_block] = t;
+            __syncthreads();
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < kNW; ++w) tot += rd[w];
+            parity ^= 1;
+            return tot;
+        } else {
+            return t;
+        }
+    };
 
     for (;;) {
         int qi;
@@ -302,12 +342,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
             if (lane == 0) q = atomicAdd(a.queue, 1);
             qi = __shfl_sync(kFull, q, 0);
         }
-        if (qi >= a.count) break;
-        const int64_t u = kFree ? (int64_t)qi : (int64_t)a.units[qi];
+        if (qi >= count) break;
+        const int64_t u = kMode == kModeFree ? (int64_t)qi : (int64_t)a.units[qi];
         const int64_t base = a.ptr[u];
         const int L = (int)(a.ptr[u + 1] - base);
-        if constexpr (kFree) {
-            // no length buckets on this path: a unit beyond NT*K nonzeros is refused
+        const int64_t perm_unit = a.unit_ids ? a.unit_ids[u] : u;
+        if constexpr (kMode != kModeHalf) {
+            // no host-side length buckets on these paths: a unit beyond NT*K nonzeros is refused
             if (L > NT * K || L < 0) {
                 if (tid_g == 0) atomicOr(a.err, 4);
                 continue;
@@ -320,7 +361,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
             x_init[k] = xv;
             xpos[k] = xv > 0.f ? 1 : 0;
         }
-        if constexpr (kCta) __syncthreads(); else __syncwarp();
+        group_sync();
 
         // ---- stage A rows, x_p, and the per-nonzero state
         float xr[K], vr[K], wr[K], qr[K];
@@ -351,107 +392,165 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                 }
             }
         }
-        // ---- coordinate order (warp 0; its staging rows hold the words)
-        if (warp_in_group == 0) {
-            ids_words_warp(words, r, u, a.sweep, a.side, a.perm_mode, a.seed, lane);
-            __syncwarp();
-            if (lane == 0) fisher_yates(perm, words, r);
-            __syncwarp();
-        }
-        if constexpr (kCta) __syncthreads(); else __syncwarp();
 
-        // ---- Algorithm 2 coordinate loop
-        // Each thread copies the tile entries it owns for the coordinate D-1
-        // positions ahead into its ring slots (cp.async; no other thread
-        // reads them), so the column is in shared memory when its turn comes.
-        auto issue = [&](int pos) {
-            if (pos < r) {
-                const float *col = tile + (int64_t)perm[pos] * lcap + tid_g;
-                float *dst = myring + (pos % D) * K * NT;
+        // ---- one pass of Algorithm 2 over the unit's coordinates (order of `sweep`)
+        auto run_coordinates = [&](int64_t sweep) {
+            if (warp_in_group == 0) {
+                ids_words_warp(words, r, perm_unit, sweep, a.side, a.perm_mode, a.seed, lane);
+                __syncwarp();
+                if (lane == 0) fisher_yates(perm, words, r);
+                __syncwarp();
+            }
+            group_sync();
+            // Each thread copies the tile entries it owns for the coordinate D-1
+            // positions ahead into its ring slots (cp.async; no other thread
+            // reads them), so the column is in shared memory when its turn comes.
+            auto issue = [&](int pos) {
+                if (pos < r) {
+                    const float *col = tile + (int64_t)perm[pos] * lcap + tid_g;
+                    float *dst = myring + (pos % D) * K * NT;
+#pragma unroll
+                    for (int s = 0; s < K; ++s)
+                        if (s < ks) cp_async4(dst + s * NT, col + NT * s, tid_g + NT * s < L ? 4 : 0);
+                }
+                cp_async_commit();
+            };
+            auto reduce = [&](float sg, float sh) -> float2 {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sg += __shfl_xor_sync(kFull, sg, o);
+                    sh += __shfl_xor_sync(kFull, sh, o);
+                }
+                if constexpr (kCta) {
+                    float2 *rb = red + parity * kNW;
+                    if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
+                    __syncthreads();
+                    float tg = 0.f, th = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kNW; ++w) {
+                        const float2 v = rb[w];
+                        tg += v.x;
+                        th += v.y;
+                    }
+                    parity ^= 1;
+                    return make_float2(tg, th);
+                } else {
+                    return make_float2(sg, sh);
+                }
+            };
+#pragma unroll
+            for (int i = 0; i < D - 1; ++i) issue(i);
+            for (int kk = 0; kk < r; ++kk) {
+                issue(kk + D - 1);
+                cp_async_wait<D - 1>();
+                const float *ac = myring + (kk % D) * K * NT;
+                const int k = perm[kk];
+                auto eval = [&]() -> float2 {
+                    float sg = 0.f, sh = 0.f;
+#pragma unroll
+                    for (int s = 0; s < K; ++s) {
+                        if (s < ks) {
+                            const float av = ac[s * NT];
+                            sg = fmaf(wr[s], av, sg);
+                            sh = fmaf(qr[s] * av, av, sh);
+                        }
+                    }
+                    return reduce(sg, sh);
+                };
+                auto update = [&](float d, int dc) {
+#pragma unroll
+                    for (int s = 0; s < K; ++s) {
+                        if (s < ks) {
+                            xr[s] = step_x(xr[s], ac[s * NT], d, dc, cr[s]);
+                            const float ri = recip(xr[s] + eps_div);
+                            wr[s] = vr[s] * ri;
+                            qr[s] = wr[s] * ri;
+                        }
+                    }
+                };
+                const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+                if (tid_g == 0) x_out[k] = xk;
+            }
+            cp_async_wait<0>();
+        };
+
+        if constexpr (kMode == kModeFold) {
+            // The column objective: Eq. 1's data term over the column's nonzeros
+            // (FP32 terms at the current x_p, FP64 sum) plus the linear and
+            // regularization terms of its r coordinates (FP64).
+            auto column_objective = [&]() -> double {
+                float t = 0.f;
 #pragma unroll
                 for (int s = 0; s < K; ++s)
-                    if (s < ks) cp_async4(dst + s * NT, col + NT * s, tid_g + NT * s < L ? 4 : 0);
-            }
-            cp_async_commit();
-        };
-        auto reduce = [&](float sg, float sh) -> float2 {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sg += __shfl_xor_sync(kFull, sg, o);
-                sh += __shfl_xor_sync(kFull, sh, o);
-            }
-            if constexpr (kCta) {
-                float2 *rb = red + parity * kNW;
-                if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
-                __syncthreads();
-                float tg = 0.f, th = 0.f;
-#pragma unroll
-                for (int w = 0; w < kNW; ++w) {
-                    const float2 v = rb[w];
-                    tg += v.x;
-                    th += v.y;
+                    if (s < ks) t += kl_term(vr[s], xr[s], eps_div);
+                double d = (double)t;
+                for (int k = tid_g; k < r; k += NT) {
+                    const double f = (double)x_init[k];
+                    d += a.sumA64[k] * f + 0.5 * (double)a.alpha * f * f + (double)a.beta * fabs(f);
                 }
-                parity ^= 1;
-                return make_float2(tg, th);
-            } else {
-                return make_float2(sg, sh);
-            }
-        };
-#pragma unroll
-        for (int i = 0; i < D - 1; ++i) issue(i);
-        for (int kk = 0; kk < r; ++kk) {
-            issue(kk + D - 1);
-            cp_async_wait<D - 1>();
-            const float *ac = myring + (kk % D) * K * NT;
-            const int k = perm[kk];
-            auto eval = [&]() -> float2 {
-                float sg = 0.f, sh = 0.f;
+                return group_sum_d(d);
+            };
+            // Algorithm 2's first step at the start of a later pass: x_p from the
+            // tile and the current coordinates, in the staging order.
+            auto recompute = [&]() {
 #pragma unroll
                 for (int s = 0; s < K; ++s) {
                     if (s < ks) {
-                        const float av = ac[s * NT];
-                        sg = fmaf(wr[s], av, sg);
-                        sh = fmaf(qr[s] * av, av, sh);
+                        const int p = tid_g + NT * s;
+                        if (p < L) {
+                            const float *col = tile + p;
+                            float acc = 0.f;
+                            int cnt = 0;
+#pragma unroll 4
+                            for (int k = 0; k < r; ++k) {
+                                const float av = col[(int64_t)k * lcap];
+                                const float xv = x_init[k];
+                                acc = fmaf(av, xv, acc);
+                                cnt += (av > 0.f && xv > 0.f) ? 1 : 0;
+                            }
+                            const float x_l = cnt == 0 ? 0.f : acc;
+                            xr[s] = x_l;
+                            cr[s] = cnt;
+                            const float ri = recip(x_l + eps_div);
+                            wr[s] = vr[s] * ri;
+                            qr[s] = wr[s] * ri;
+                        }
                     }
                 }
-                return reduce(sg, sh);
             };
-            auto update = [&](float d, int dc) {
+            group_sync();
+            double prev = column_objective();
+            int done_sweeps = 0;
+            while (done_sweeps < a.max_sweeps) {
+                run_coordinates(done_sweeps);
+                group_sync();
+                for (int k = tid_g; k < r; k += NT) x_init[k] = x_out[k];
+                group_sync();
+                ++done_sweeps;
+                recompute();
+                const double cur = column_objective();
+                const bool settled = fabs(prev - cur) <= a.rel_tol * fabs(prev);
+                prev = cur;
+                if (settled) break;
+            }
+            group_sync();
+            for (int k = tid_g; k < r; k += NT) x_out[k] = x_init[k];
+            if (tid_g == 0) {
+                a.sweeps_done[u] = done_sweeps;
+                a.unit_final[u] = prev;
+            }
+        } else {
+            run_coordinates(a.sweep);
+            if (a.unit_obj) {
+                float t = 0.f;
 #pragma unroll
-                for (int s = 0; s < K; ++s) {
-                    if (s < ks) {
-                        xr[s] = step_x(xr[s], ac[s * NT], d, dc, cr[s]);
-                        const float ri = recip(xr[s] + eps_div);
-                        wr[s] = vr[s] * ri;
-                        qr[s] = wr[s] * ri;
-                    }
-                }
-            };
-            const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
-            if (tid_g == 0) x_out[k] = xk;
-        }
-        cp_async_wait<0>();
-        if (a.unit_obj) {
-            float t = 0.f;
-#pragma unroll
-            for (int s = 0; s < K; ++s)
-                if (s < ks) t += kl_term(vr[s], xr[s], eps_div);
-            double dt = warp_sum_d((double)t);
-            if constexpr (kCta) {
-                double *rd = reinterpret_cast<double *>(red + parity * kNW);
-                if (lane == 0) rd[warp_in_block] = dt;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    double tot = 0.0;
-                    for (int w = 0; w < kNW; ++w) tot += rd[w];
-                    a.unit_obj[u] = tot;
-                }
-                parity ^= 1;
-            } else if (lane == 0) {
-                a.unit_obj[u] = dt;
+                for (int s = 0; s < K; ++s)
+                    if (s < ks) t += kl_term(vr[s], xr[s], eps_div);
+                const double tot = group_sum_d((double)t);
+                if (tid_g == 0) a.unit_obj[u] = tot;
             }
         }
-        if constexpr (kCta) __syncthreads(); else __syncwarp();
+        group_sync();
         discard_tile(tile, r, L, lcap, tid_g, NT);
         for (int k = tid_g; k < r; k += NT) {
             const float xv = x_out[k];
@@ -1130,6 +1229,268 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
 
 
 // ---------------------------------------------------------------------------
+// Fold-in (nmfkl_foldin): the F half alone under the context's fixed W, each
+// new column running its own passes of Algorithm 2 until its objective
+// settles. Columns are sorted into length classes on the device, so that the
+// whole launch sequence (sums of W, classification, one persistent launch per
+// class, output transpose) depends on no host-side knowledge of the lengths
+// and is captured once into a CUDA graph.
+// ---------------------------------------------------------------------------
+namespace {
+
+const KernelKind kFoldTable[kFoldKinds] = {
+    {(const void *)sweep_kernel<32, 1, 8, kModeFold>, 32, 1, 1, 8, "foldin_warp_k1"},
+    {(const void *)sweep_kernel<32, 2, 8, kModeFold>, 32, 2, 1, 8, "foldin_warp_k2"},
+    {(const void *)sweep_kernel<32, 4, 8, kModeFold>, 32, 4, 1, 8, "foldin_warp_k4"},
+    {(const void *)sweep_kernel<32, 8, 6, kModeFold>, 32, 8, 1, 6, "foldin_warp_k8"},
+    {(const void *)sweep_kernel<32, 16, 4, kModeFold>, 32, 16, 1, 4, "foldin_warp_k16"},
+    {(const void *)sweep_kernel<128, 8, 8, kModeFold>, 128, 8, 1, 8, "foldin_cta128_k8"},
+    {(const void *)sweep_kernel<256, 8, 6, kModeFold>, 256, 8, 1, 6, "foldin_cta256_k8"},
+    {(const void *)sweep_kernel<512, 8, 4, kModeFold>, 512, 8, 1, 4, "foldin_cta512_k8"},
+    {(const void *)sweep_kernel<512, 16, 3, kModeFold>, 512, 16, 1, 3, "foldin_cta512_k16"},
+};
+
+__host__ __device__ inline int fold_kind_for_length(int64_t L) {
+    constexpr int cap[kFoldKinds] = {32, 64, 128, 256, 512, 1024, 2048, 4096, 8192};
+    for (int i = 0; i < kFoldKinds; ++i)
+        if (L <= cap[i]) return i;
+    return -1;
+}
+
+// Sorts the columns into the length classes; a column longer than the last
+// class sets error bit 4 and is left out.
+__global__ void fold_bucketize_kernel(const int64_t *colptr, int64_t m, int32_t *lists, int64_t cap_m,
+                                      int32_t *counts, int32_t *err) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int kind = fold_kind_for_length(colptr[j + 1] - colptr[j]);
+        if (kind < 0) {
+            atomicOr(err, 4);
+            continue;
+        }
+        const int pos = atomicAdd(&counts[kind], 1);
+        lists[(int64_t)kind * cap_m + pos] = (int32_t)j;
+    }
+}
+
+HalfArgs fold_args(nmfkl_ctx *c, FoldState &f, bool with_ids, double rel_tol, int32_t max_sweeps) {
+    HalfArgs a{};
+    a.ptr = f.colptr;
+    a.idx = f.rowidx;
+    a.val = f.val;
+    a.At = c->Wt;
+    a.X = f.Ft;
+    a.sumA = c->sumW;
+    a.r = c->p.r;
+    a.ldr = c->ldr;
+    a.alpha = (float)c->p.alpha_F;
+    a.beta = (float)c->p.beta_F;
+    a.eps_grad = (float)c->p.eps_grad;
+    a.eps_div = (float)c->p.eps_div;
+    a.eps_x = (float)c->p.eps_x;
+    a.max_inner = c->p.max_inner;
+    a.grad_mode = c->p.grad_mode;
+    a.break_mode = c->p.break_mode;
+    a.perm_mode = c->p.perm_mode;
+    a.seed = c->p.seed;
+    a.side = 0;
+    a.scratch = f.scratch;
+    a.counters = c->counters;
+    a.err = f.ctl + 2 * kFoldKinds;
+    a.unit_ids = with_ids ? f.ids : nullptr;
+    a.max_sweeps = max_sweeps;
+    a.rel_tol = rel_tol;
+    a.sumA64 = c->dsum[0];
+    a.sweeps_done = f.sweeps;
+    a.unit_final = f.obj;
+    return a;
+}
+
+// The fold-in launch sequence on `st` (capturable: no host synchronization,
+// no allocation).
+cudaError_t fold_enqueue(nmfkl_ctx *c, cudaStream_t st, int64_t m_new, bool with_ids, double rel_tol,
+                         int32_t max_sweeps, bool timed) {
+    FoldState &f = *c->fold;
+    launch_colsum_raw(st, c->Wt, c->n, c->ldr, c->p.r, c->dpart, c->sumW, c->dsum[0]);
+    cudaError_t e = cudaMemsetAsync(f.ctl, 0, sizeof(int32_t) * (2 * kFoldKinds + 1), st);
+    if (e != cudaSuccess) return e;
+    if (m_new > 0) {
+        const int blocks = (int)std::min<int64_t>((m_new + 255) / 256, 4096);
+        fold_bucketize_kernel<<<blocks, 256, 0, st>>>(f.colptr, m_new, f.lists, f.cap_m, f.ctl, f.ctl + 2 * kFoldKinds);
+    }
+    HalfArgs a = fold_args(c, f, with_ids, rel_tol, max_sweeps);
+    for (int kind = 0; kind < kFoldKinds && m_new > 0; ++kind) {
+        a.units = f.lists + (int64_t)kind * f.cap_m;
+        a.count = 0;
+        a.count_dev = f.ctl + kind;
+        a.queue = f.ctl + kFoldKinds + kind;
+        a.slot_floats = f.slot_floats[kind];
+        a.lcap = f.lcap[kind];
+        void *args[] = {&a};
+        const int tok = timed ? timer_begin(c, kFoldTable[kind].name) : -1;
+        e = cudaLaunchKernel(kFoldTable[kind].fn, dim3(f.grid[kind]), dim3(f.block[kind]), args, f.smem[kind], st);
+        if (timed) timer_end(c, tok);
+        if (e != cudaSuccess) return e;
+    }
+    if (m_new > 0) launch_from_unit_major_raw(st, f.Ft, f.Fout, c->p.r, m_new, c->ldr);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int foldin_kind_for_length(int64_t L) { return fold_kind_for_length(L); }
+
+void free_fold(nmfkl_ctx *c) {
+    FoldState *f = c->fold;
+    if (!f) return;
+    if (f->graph) cudaGraphExecDestroy(f->graph);
+    if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
+    cudaFree(f->colptr); cudaFree(f->ids); cudaFree(f->rowidx); cudaFree(f->val); cudaFree(f->Ft);
+    cudaFree(f->Fout); cudaFree(f->lists); cudaFree(f->ctl); cudaFree(f->sweeps); cudaFree(f->obj);
+    cudaFree(f->scratch);
+    delete f;
+    c->fold = nullptr;
+}
+
+// Sizes the per-class launches and the tile scratch once per context.
+nmfkl_status fold_plan(nmfkl_ctx *c) {
+    FoldState &f = *c->fold;
+    if (f.planned) return NMFKL_OK;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    optin -= 1024;
+    const int r = c->p.r, ldr = c->ldr;
+    int64_t scratch = 0;
+    for (int kind = 0; kind < kFoldKinds; ++kind) {
+        const KernelKind &kk = kFoldTable[kind];
+        const bool cta = kk.nt > 32;
+        const size_t gbytes = ring_layout(r, ldr, kk.nt, kk.k, kk.d, cta).bytes;
+        int gpb = 1;
+        if (!cta) {
+            gpb = 8;
+            while (gpb > 1 && gbytes * gpb > (size_t)optin) --gpb;
+        }
+        f.block[kind] = cta ? kk.nt : 32 * gpb;
+        f.smem[kind] = gbytes * (cta ? 1 : gpb);
+        if (f.smem[kind] > (size_t)optin) {
+            c->err = "fold-in: shared memory plan exceeds the device limit";
+            return NMFKL_EINVAL;
+        }
+        if (!cuda_ok(c, cudaFuncSetAttribute(kk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem[kind]),
+                     "fold-in smem attribute"))
+            return NMFKL_ECUDA;
+        int per_sm = 0;
+        if (!cuda_ok(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kk.fn, f.block[kind], f.smem[kind]),
+                     "fold-in occupancy"))
+            return NMFKL_ECUDA;
+        if (per_sm < 1) {
+            c->err = std::string("fold-in kernel ") + kk.name + " cannot be resident";
+            return NMFKL_EINVAL;
+        }
+        f.grid[kind] = per_sm * c->num_sms;
+        f.groups[kind] = f.grid[kind] * gpb;
+        f.lcap[kind] = kk.nt * kk.k;
+        f.slot_floats[kind] = ((int64_t)r * f.lcap[kind] + 63) / 64 * 64;
+        scratch = std::max<int64_t>(scratch, f.slot_floats[kind] * f.groups[kind]);
+    }
+    if (!cuda_ok(c, cudaMalloc(&f.scratch, sizeof(float) * (size_t)scratch), "fold-in scratch")) return NMFKL_ENOMEM;
+    if (!cuda_ok(c, cudaMemset(f.scratch, 0, sizeof(float) * (size_t)scratch), "zero fold-in scratch"))
+        return NMFKL_ECUDA;
+    f.scratch_floats = scratch;
+    if (!cuda_ok(c, cudaStreamCreateWithFlags(&f.cap_stream, cudaStreamNonBlocking), "fold-in capture stream"))
+        return NMFKL_ECUDA;
+    f.planned = true;
+    return NMFKL_OK;
+}
+
+nmfkl_status foldin_run(nmfkl_ctx *c, int64_t m_new, bool with_ids, double rel_tol, int32_t max_sweeps,
+                        bool use_graph) {
+    nmfkl_status st = fold_plan(c);
+    if (st != NMFKL_OK) return st;
+    FoldState &f = *c->fold;
+    if (!use_graph) {
+        return cuda_ok(c, fold_enqueue(c, c->stream, m_new, with_ids, rel_tol, max_sweeps, c->timing), "fold-in launch")
+                   ? NMFKL_OK
+                   : NMFKL_ECUDA;
+    }
+    if (!f.graph || f.graph_m != m_new || f.graph_ids != with_ids || f.graph_tol != rel_tol ||
+        f.graph_sweeps != max_sweeps) {
+        if (f.graph) {
+            cudaGraphExecDestroy(f.graph);
+            f.graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        if (!cuda_ok(c, cudaStreamBeginCapture(f.cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture"))
+            return NMFKL_ECUDA;
+        const cudaError_t e = fold_enqueue(c, f.cap_stream, m_new, with_ids, rel_tol, max_sweeps, false);
+        const cudaError_t e2 = cudaStreamEndCapture(f.cap_stream, &g);
+        if (!cuda_ok(c, e, "fold-in capture") || !cuda_ok(c, e2, "end capture")) {
+            if (g) cudaGraphDestroy(g);
+            return NMFKL_ECUDA;
+        }
+        const cudaError_t e3 = cudaGraphInstantiate(&f.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (!cuda_ok(c, e3, "instantiate fold-in graph")) {
+            f.graph = nullptr;
+            return NMFKL_ECUDA;
+        }
+        f.graph_m = m_new;
+        f.graph_ids = with_ids;
+        f.graph_tol = rel_tol;
+        f.graph_sweeps = max_sweeps;
+    }
+    const int tok = timer_begin(c, "foldin_graph");
+    const cudaError_t e = cudaGraphLaunch(f.graph, c->stream);
+    timer_end(c, tok);
+    return cuda_ok(c, e, "fold-in graph launch") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+// The plain scheme the batched launch is measured against: one launch per
+// column (the same kernel, one group), in column order.
+nmfkl_status foldin_per_doc(nmfkl_ctx *c, int64_t m_new, double rel_tol, int32_t max_sweeps) {
+    nmfkl_status st = fold_plan(c);
+    if (st != NMFKL_OK) return st;
+    FoldState &f = *c->fold;
+    std::vector<int64_t> ptr(m_new + 1);
+    if (!cuda_ok(c, cudaMemcpyAsync(ptr.data(), f.colptr, sizeof(int64_t) * (m_new + 1), cudaMemcpyDeviceToHost,
+                                    c->stream),
+                 "copy fold-in offsets") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "fold-in offsets sync"))
+        return NMFKL_ECUDA;
+    // per column: a one-entry unit list (the column itself) and its own work counter
+    std::vector<int32_t> iota(m_new);
+    for (int64_t j = 0; j < m_new; ++j) iota[j] = (int32_t)j;
+    if (!cuda_ok(c, cudaMemcpyAsync(f.lists, iota.data(), sizeof(int32_t) * m_new, cudaMemcpyHostToDevice, c->stream),
+                 "fold-in unit ids") ||
+        !cuda_ok(c, cudaMemsetAsync(f.lists + f.cap_m, 0, sizeof(int32_t) * m_new, c->stream), "fold-in counters") ||
+        !cuda_ok(c, cudaMemsetAsync(f.ctl, 0, sizeof(int32_t) * (2 * kFoldKinds + 1), c->stream), "fold-in flags") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "fold-in per-column setup"))
+        return NMFKL_ECUDA;
+    launch_colsum_raw(c->stream, c->Wt, c->n, c->ldr, c->p.r, c->dpart, c->sumW, c->dsum[0]);
+    HalfArgs a = fold_args(c, f, false, rel_tol, max_sweeps);
+    a.count = 1;
+    for (int64_t j = 0; j < m_new; ++j) {
+        const int kind = fold_kind_for_length(ptr[j + 1] - ptr[j]);
+        if (kind < 0) {
+            c->err = "fold-in: a column has more nonzeros than the longest length class";
+            return NMFKL_EINVAL;
+        }
+        const KernelKind &kk = kFoldTable[kind];
+        a.units = f.lists + j;
+        a.queue = f.lists + f.cap_m + j;
+        a.slot_floats = f.slot_floats[kind];
+        a.lcap = f.lcap[kind];
+        void *args[] = {&a};
+        if (!cuda_ok(c, cudaLaunchKernel(kk.fn, dim3(1), dim3(kk.nt), args,
+                                         ring_layout(c->p.r, c->ldr, kk.nt, kk.k, kk.d, kk.nt > 32).bytes, c->stream),
+                     kk.name))
+            return NMFKL_ECUDA;
+    }
+    launch_from_unit_major_raw(c->stream, f.Ft, f.Fout, c->p.r, m_new, c->ldr);
+    return cuda_ok(c, cudaGetLastError(), "fold-in per-column launches") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+
+// ---------------------------------------------------------------------------
 // Allocation-free F half (nmfkl_sweep_F_noalloc in include/nmfkl.h).
 //
 // Its scratch is the file-scope array below, held by every GPU that loads
@@ -1159,10 +1520,10 @@ struct NoAllocCtl {  // lives at the start of the control block
 };
 
 const KernelKind kFreeKinds[] = {
-    {(const void *)sweep_kernel<32, 1, 8, true>, 32, 1, 1, 8, "sweep_warp_k1_noalloc"},
-    {(const void *)sweep_kernel<32, 2, 8, true>, 32, 2, 1, 8, "sweep_warp_k2_noalloc"},
-    {(const void *)sweep_kernel<32, 4, 8, true>, 32, 4, 1, 8, "sweep_warp_k4_noalloc"},
-    {(const void *)sweep_kernel<32, 8, 6, true>, 32, 8, 1, 6, "sweep_warp_k8_noalloc"},
+    {(const void *)sweep_kernel<32, 1, 8, kModeFree>, 32, 1, 1, 8, "sweep_warp_k1_noalloc"},
+    {(const void *)sweep_kernel<32, 2, 8, kModeFree>, 32, 2, 1, 8, "sweep_warp_k2_noalloc"},
+    {(const void *)sweep_kernel<32, 4, 8, kModeFree>, 32, 4, 1, 8, "sweep_warp_k4_noalloc"},
+    {(const void *)sweep_kernel<32, 8, 6, kModeFree>, 32, 8, 1, 6, "sweep_warp_k8_noalloc"},
 };
 }  // namespace
 
