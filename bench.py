@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["sweep", "foldin", "serve"], default="sweep",
+                    help="sweep: the factorization step (default); foldin: batched fold-in of new documents; "
+                         "serve: the request loop under Poisson arrivals")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per arrival rate")
+    ap.add_argument("--slots", type=int, default=4, help="serve: worker slots")
+    ap.add_argument("--docs", type=int, default=10_000, help="fold-in: documents per batch")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
     ap.add_argument("--r", type=int, default=100)
     ap.add_argument("--seed", type=int, default=0)
@@ -394,10 +400,207 @@ def e2e_run(args, V, nk, torch, local, barrier, pg):
             "seconds": dt, "scope": "one fit job: upload V, random start, K steps, download W and F"}
 
 
+# --------------------------------------------------------------------------- fold-in
+def run_foldin(args):
+    """Batched fold-in of new documents under a fixed W: one launch sequence per
+    batch captured in a CUDA graph, against the plain scheme of one launch per
+    document on the same inputs (identical results, checked)."""
+    import torch
+    import paper_1604_04026_gb300 as nk
+    from paper_1604_04026_gb300 import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    threads = args.threads or os.cpu_count() or 1
+    n, K = 30_000, args.r
+    topics, V = synth.foldin_docs(n, args.docs, K, seed=args.seed, threads=threads)
+    model = nk.NMFKL(n, 1, r=K, seed=args.seed, device=local)
+    model.init(topics, np.zeros((K, 1), dtype=np.float32))
+    d = {k: torch.from_numpy(getattr(V, k)).cuda() for k in ("colptr", "rowidx", "val")}
+    F0 = torch.from_numpy(synth.uniform_init(K, V.m, args.seed, 2)).cuda()
+
+    # the per-document scheme runs on the first `sample` documents (their results
+    # do not depend on the batch they are in)
+    sample = min(V.m, 500)
+    ds = {"colptr": d["colptr"][:sample + 1], "rowidx": d["rowidx"][:int(V.colptr[sample])],
+          "val": d["val"][:int(V.colptr[sample])]}
+    F0s = F0[:, :sample].contiguous()
+
+    def run(mode):
+        if mode == 2:
+            return model.foldin(colptr=ds["colptr"], rowidx=ds["rowidx"], val=ds["val"], F0=F0s, rel_tol=1e-5,
+                                max_sweeps=200, launch_mode=mode)
+        return model.foldin(colptr=d["colptr"], rowidx=d["rowidx"], val=d["val"], F0=F0, rel_tol=1e-5,
+                            max_sweeps=200, launch_mode=mode)
+
+    def timed(mode, steps, warm):
+        for _ in range(warm):
+            out = run(mode)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            out = run(mode)
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps, out
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_graph, out_g = timed(0, args.steps, args.warmup)
+    clocks.stop()
+    ms_plain, out_p = timed(1, args.steps, 1)
+    ms_doc, out_d = timed(2, 1, 1)
+    same = all(torch.equal(a, b) for a, b in zip(out_g, out_p)) and \
+        torch.equal(out_g[0][:, :sample], out_d[0]) and torch.equal(out_g[1][:sample], out_d[1]) and \
+        torch.equal(out_g[2][:sample], out_d[2])
+    sweeps = out_g[1].double()
+    # end to end: host inputs and outputs through the public call
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Fh, sh, oh = model.foldin(V, F0=F0.cpu().numpy(), rel_tol=1e-5, max_sweeps=200)
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    h2d = V.colptr.nbytes + V.rowidx.nbytes + V.val.nbytes + 4 * K * V.m
+    d2h = 4 * K * V.m + 4 * V.m + 8 * V.m
+    line = {
+        "metric": "fold-in batch latency", "value": ms_graph, "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched fold-in: fixed W = the generator's %d topic-word laws over n=%d words, "
+                               "%d new documents, Pareto(5, 1.5) distinct words capped at 5000" % (K, n, V.m),
+                   "nnz": V.nnz, "rel_tol": 1e-5, "l2": "inputs smaller than L2; no flush between batches"},
+        "docs_per_s": V.m / (ms_graph / 1e3),
+        "per_document_launches": {"ms": ms_doc, "documents": sample, "ms_per_document": ms_doc / sample},
+        "speedup_vs_per_document": (ms_doc / sample) / (ms_graph / V.m),
+        "batched_without_graph_ms": ms_plain, "identical_results": bool(same),
+        "sweeps_per_doc": {"mean": float(sweeps.mean()), "max": int(sweeps.max())},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    model.close()
+    return 0
+
+
+# --------------------------------------------------------------------------- serving
+def _slice_docs(V, a, b):
+    from paper_1604_04026_gb300 import synth
+    lo, hi = int(V.colptr[a]), int(V.colptr[b])
+    return synth.from_csc(V.n, b - a, V.colptr[a:b + 1] - lo, V.rowidx[lo:hi], V.val[lo:hi])
+
+
+def serve_requests(args, pool, rng):
+    """The request mix: 80% fold-in batches of 1-2,000 documents (slices of the
+    fold-in pool), 20% factorizations with n in [500, 20000], m in [1000,
+    50000], r in [10, 100], density in [0.1, 2]% (masked Poisson low-rank
+    counts), stopping at relative change 1e-4 or 50 sweeps."""
+    from paper_1604_04026_gb300 import synth
+    reqs = []
+    for i in range(args.requests):
+        if rng.random() < 0.8:
+            size = int(rng.integers(1, 2001))
+            a = int(rng.integers(0, pool.m - size))
+            reqs.append(("foldin", _slice_docs(pool, a, a + size), None, None))
+        else:
+            n, m = int(rng.integers(500, 20001)), int(rng.integers(1000, 50001))
+            r, dens = int(rng.integers(10, 101)), float(rng.uniform(0.001, 0.02))
+            V = synth.poisson_lowrank_sparse(n, m, min(r, 20), density=dens, seed=args.seed * 1000 + i)
+            reqs.append(("fit", V, r, args.seed * 1000 + i))
+    return reqs
+
+
+def run_serve(args):
+    """The serving loop: capacity from a closed-loop run of the request list,
+    then open-loop Poisson arrivals at 50, 80 and 95% of it; latency is
+    submit to completion as the server measures it."""
+    import torch
+    import paper_1604_04026_gb300 as nk
+    from paper_1604_04026_gb300 import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    threads = args.threads or os.cpu_count() or 1
+    n, K = 30_000, args.r
+    topics, pool = synth.foldin_docs(n, 40_000, K, seed=args.seed, threads=threads)
+    rng = np.random.default_rng(args.seed)
+    reqs = serve_requests(args, pool, rng)
+
+    def submit(srv, q):
+        kind, V, r, seed = q
+        if kind == "foldin":
+            return srv.submit_foldin(V, rel_tol=1e-5, max_sweeps=200)
+        return srv.submit_fit(V, r, seed=seed, rel_tol=1e-4, max_sweeps=50)
+
+    def run(srv, rate):
+        arrivals = np.zeros(len(reqs)) if rate is None else np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+        tickets = []
+        t0 = time.perf_counter()
+        for q, ta in zip(reqs, arrivals):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            while True:
+                try:
+                    tickets.append(submit(srv, q))
+                    break
+                except nk.NMFKLError as e:
+                    if e.status_name != "EBUSY":
+                        raise
+                    time.sleep(0.001)
+        for t in tickets:
+            srv.wait(t)
+            assert t.status == "OK", (t.status, t.message)
+        wall = time.perf_counter() - t0
+        lat = np.array([t.queued_ms + t.run_ms for t in tickets])
+        kinds = np.array([q[0] for q in reqs])
+
+        def pct(x):
+            return {"p50_ms": float(np.percentile(x, 50)), "p99_ms": float(np.percentile(x, 99))} if x.size else None
+        return {"requests_per_s": len(reqs) / wall, "wall_s": wall, "all": pct(lat),
+                "foldin": pct(lat[kinds == "foldin"]), "fit": pct(lat[kinds == "fit"]),
+                "mean_batch_requests": float(np.mean([t.batch_requests for t, k in zip(tickets, kinds)
+                                                      if k == "foldin"] or [0]))}
+
+    p = nk.default_params(K, seed=args.seed)
+    clocks = ClockSampler(local)
+    with nk.Server(topics, params=p, device=local, slots=args.slots) as srv:
+        run(srv, None)  # warm-up: plans, graphs, allocations
+        cap = run(srv, None)
+        capacity = cap["requests_per_s"]
+        clocks.start()
+        levels = {}
+        for f in (0.5, 0.8, 0.95):
+            levels["%d%%" % round(100 * f)] = run(srv, f * capacity)
+        clocks.stop()
+        stats = srv.stats()
+    top = levels["95%"]
+    line = {
+        "metric": "fold-in p99 latency", "value": top["foldin"]["p99_ms"], "unit": "ms", "n_gpus": 1,
+        "steps": len(reqs), "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals at 50/80/95%% of capacity, %d requests per rate: 80%% "
+                               "fold-in batches of 1-2,000 documents under W = %d topic-word laws over n=%d, 20%% "
+                               "factorizations (n 500-20,000, m 1,000-50,000, r 10-100, density 0.1-2%%)"
+                               % (len(reqs), K, n), "slots": args.slots},
+        "capacity_requests_per_s": capacity, "closed_loop": cap, "open_loop": levels, "server": stats,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "foldin":
+        return run_foldin(args)
+    if args.mode == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

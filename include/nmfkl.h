@@ -76,6 +76,13 @@ typedef struct {
                              column); 1: one order per sweep shared by every column
                              and row (Algorithm 1 draws ids once per iteration) */
     uint64_t seed;        /* Philox4x64-10 key for coordinate orders and random init */
+    int32_t list_mode;    /* how a coordinate visits the unit's nonzeros. 0 (default): per
+                             half, only the nonzeros with A_pk > 0 (per-coordinate lists
+                             built while staging) when the fixed factor is less than half
+                             dense at the nonzeros of V, else all of them (dense tile);
+                             1: always the dense tile; 2: always the lists. The sums of
+                             Eq. Partial are the same (terms with A_pk = 0 are zero); only
+                             the FP32 summation order differs. */
 } nmfkl_params;
 
 typedef struct nmfkl_ctx nmfkl_ctx;
@@ -262,6 +269,105 @@ nmfkl_status nmfkl_debug_perm(nmfkl_ctx *ctx, int64_t sweep, int32_t side, int64
 nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, int64_t m, int32_t max_len,
                                    const int64_t *colptr, const int32_t *rowidx, const float *val,
                                    const float *Wt, float *Ft, int64_t sweep, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop around one resident model W (r x n).
+ *
+ * Requests arrive at any time (nmfkl_server_submit returns at once with a
+ * ticket) and are of two kinds: fold-in of new documents under W (as
+ * nmfkl_foldin, launch mode 0) and a small full factorization of its own V
+ * (Algorithm 1 from a Uniform[0,1) start, as nmfkl_fit). `slots` worker
+ * threads each own a CUDA stream; a worker takes work from the head of one
+ * FIFO queue as soon as the memory budget admits it -- every fold-in request
+ * waiting at the head with the same rel_tol and max_sweeps, merged into one
+ * batched fold-in launch (up to max_batch_docs columns and max_batch_nnz
+ * nonzeros), or the factorization at the head -- so requests that arrive
+ * while others run are admitted as slots and memory free up, and their work
+ * overlaps on the device. A request's result is the same whatever it shares
+ * a batch or the device with: fold-in columns are keyed by their index
+ * within their own request (unit id of the coordinate orders) and draw their
+ * start from Uniform[0,1) as a batch of their own (nmfkl_init's rule with
+ * which = 2); a factorization runs in a context of its own.
+ *
+ * Memory admission: each request is charged an estimate of the device bytes
+ * it holds while it runs (inputs, outputs, factors, tiles); work is admitted
+ * while the charges of running work plus the head's stay within mem_budget
+ * (a request above the whole budget is refused with EINVAL at submit). The
+ * per-slot state (W copy, fold-in tiles) is allocated at creation and not
+ * charged. submit returns EBUSY when max_pending requests already wait.
+ * ------------------------------------------------------------------------ */
+typedef struct nmfkl_server nmfkl_server;
+
+typedef struct {
+    int32_t device;
+    int32_t slots;           /* worker threads / streams; default 4 */
+    int64_t mem_budget;      /* bytes of admitted work in flight; default 16 GiB */
+    int32_t max_pending;     /* queued requests before EBUSY; default 4096 */
+    int32_t max_batch_docs;  /* fold-in columns merged into one batch; default 20000 */
+    int64_t max_batch_nnz;   /* fold-in nonzeros merged into one batch; default 2^26 */
+} nmfkl_server_cfg;
+
+enum { NMFKL_REQ_FOLDIN = 0, NMFKL_REQ_FIT = 1 };
+
+/* One request. Inputs are host memory and are copied at submit. Outputs are
+ * host memory the caller keeps valid until the request is collected (poll or
+ * wait returned NMFKL_OK for it); any output may be NULL. */
+typedef struct {
+    int32_t kind;                 /* NMFKL_REQ_FOLDIN or NMFKL_REQ_FIT */
+    int64_t n, m, nnz;            /* V is n x m (fold-in: n = the model's n, m documents) */
+    const int64_t *colptr;        /* CSC of V as in nmfkl_set_data */
+    const int32_t *rowidx;
+    const float *val;
+    int32_t r;                    /* fit: latent factors (fold-in: the model's r) */
+    uint64_t seed;                /* fit: seed of the start and the coordinate orders */
+    double rel_tol;               /* stopping tolerance (fold-in: per column; fit: Algorithm 1) */
+    int32_t max_sweeps;
+    float *F_out;                 /* r x m row-major */
+    float *W_out;                 /* fit: r x n row-major */
+    int32_t *sweeps_out;          /* fold-in: m entries; fit: 1 */
+    double *obj_out;              /* fold-in: m column objectives; fit: 1 (Eq. 1 at the end) */
+} nmfkl_request;
+
+typedef struct {
+    nmfkl_status status;          /* the request's own outcome */
+    double queued_ms;             /* submit to admission */
+    double run_ms;                /* admission to completion */
+    int32_t batch_requests;       /* requests in the batch it ran in (1 for a fit) */
+    char message[160];            /* on failure, what failed ("" on success) */
+} nmfkl_result;
+
+typedef struct {
+    int64_t pending, mem_in_use, batches, batched_requests;
+} nmfkl_server_stats_t;
+
+/* Fills the defaults listed above. */
+void nmfkl_server_default_cfg(nmfkl_server_cfg *cfg);
+
+/* Starts the workers with W (host, r x n row-major, copied to every slot) and
+ * the parameters of Algorithms 1 and 2 (fold-in uses alpha_F, beta_F). */
+nmfkl_status nmfkl_server_create(const nmfkl_server_cfg *cfg, const nmfkl_params *p, int64_t n,
+                                 const float *W, nmfkl_server **out);
+
+/* Queues a request; *ticket identifies it. EBUSY: the queue is full now
+ * (retry later); EINVAL: malformed, or larger than the whole budget. Data
+ * errors found later (unsorted indices, zero values, a column beyond 8192
+ * nonzeros) are reported in the request's result status. */
+nmfkl_status nmfkl_server_submit(nmfkl_server *s, const nmfkl_request *req, uint64_t *ticket);
+
+/* Non-blocking: OK (and *res filled, the ticket retired) once the request is
+ * done, EBUSY while it waits or runs, EINVAL for an unknown ticket. */
+nmfkl_status nmfkl_server_poll(nmfkl_server *s, uint64_t ticket, nmfkl_result *res);
+
+/* Blocks until the request is done, then as poll. */
+nmfkl_status nmfkl_server_wait(nmfkl_server *s, uint64_t ticket, nmfkl_result *res);
+
+/* Queue length, charged memory, and how many fold-in batches have run and
+ * how many requests they held. */
+nmfkl_status nmfkl_server_stats(nmfkl_server *s, nmfkl_server_stats_t *out);
+
+/* Finishes the work that is running, drops what still waits, joins the
+ * workers and frees everything. */
+void nmfkl_server_destroy(nmfkl_server *s);
 
 #ifdef __cplusplus
 }

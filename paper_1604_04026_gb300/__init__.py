@@ -22,7 +22,7 @@ import numpy as np
 from . import _native, synth
 from ._native import Counters, Params
 
-__all__ = ["NMFKL", "NMFKLError", "Params", "default_params", "synth"]
+__all__ = ["NMFKL", "NMFKLError", "Params", "Server", "default_params", "synth"]
 
 
 class NMFKLError(RuntimeError):
@@ -246,3 +246,112 @@ class NMFKL:
         """Device orders: out_dev[c, :] = ids of unit cols_dev[c] (CUDA tensors)."""
         self._check(self._lib.nmfkl_debug_perm(self._h, sweep, side, int(cols_dev.numel()),
                                                cols_dev.data_ptr(), out_dev.data_ptr()), "debug_perm")
+
+
+class Ticket:
+    """A submitted serving request and the host arrays its results land in."""
+
+    def __init__(self, ticket, kind, keep, F, W, sweeps, obj):
+        self.id, self.kind, self._keep = ticket, kind, keep
+        self.F, self.W, self.sweeps, self.obj = F, W, sweeps, obj
+        self.status = None
+        self.message = ""
+        self.queued_ms = self.run_ms = None
+        self.batch_requests = None
+
+    def _set(self, res):
+        self.status = _native.STATUS_NAMES.get(res.status, str(res.status))
+        self.message = res.message.decode(errors="replace")
+        self.queued_ms, self.run_ms, self.batch_requests = res.queued_ms, res.run_ms, res.batch_requests
+        self._keep = None
+
+
+class Server:
+    """Serving loop around one resident model W (r x n): fold-in requests and
+    small factorizations, admitted as slots and memory free up (nmfkl_server_*)."""
+
+    def __init__(self, W, params: Params | None = None, r: int | None = None, device: int = 0, slots: int = 4,
+                 mem_budget: int = 16 << 30, max_pending: int = 4096, max_batch_docs: int = 20000,
+                 max_batch_nnz: int = 1 << 26, **kw):
+        self._lib = _native.load()
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        if params is None:
+            params = default_params(r or W.shape[0], **kw)
+        self.params, self.r, self.n = params, int(params.r), int(W.shape[1])
+        cfg = _native.ServerCfg()
+        self._lib.nmfkl_server_default_cfg(ctypes.byref(cfg))
+        cfg.device, cfg.slots, cfg.mem_budget, cfg.max_pending = device, slots, mem_budget, max_pending
+        cfg.max_batch_docs, cfg.max_batch_nnz = max_batch_docs, max_batch_nnz
+        h = ctypes.c_void_p()
+        st = self._lib.nmfkl_server_create(ctypes.byref(cfg), ctypes.byref(params), self.n, W.ctypes.data,
+                                           ctypes.byref(h))
+        if st != 0:
+            raise NMFKLError(st, "nmfkl_server_create failed")
+        self._h = h
+
+    def _submit(self, kind, V, r, seed, rel_tol, max_sweeps):
+        colptr = np.ascontiguousarray(V.colptr, dtype=np.int64)
+        rowidx = np.ascontiguousarray(V.rowidx, dtype=np.int32)
+        val = np.ascontiguousarray(V.val, dtype=np.float32)
+        F = np.zeros((r, V.m), dtype=np.float32)
+        W = np.zeros((r, V.n), dtype=np.float32) if kind == 1 else None
+        sweeps = np.zeros(max(V.m, 1) if kind == 0 else 1, dtype=np.int32)
+        obj = np.zeros(max(V.m, 1) if kind == 0 else 1, dtype=np.float64)
+        q = _native.Request(kind=kind, n=V.n, m=V.m, nnz=int(V.nnz), colptr=colptr.ctypes.data,
+                            rowidx=rowidx.ctypes.data, val=val.ctypes.data, r=r, seed=seed, rel_tol=rel_tol,
+                            max_sweeps=max_sweeps, F_out=F.ctypes.data, W_out=W.ctypes.data if W is not None else None,
+                            sweeps_out=sweeps.ctypes.data, obj_out=obj.ctypes.data)
+        t = ctypes.c_uint64()
+        st = self._lib.nmfkl_server_submit(self._h, ctypes.byref(q), ctypes.byref(t))
+        if st != 0:
+            raise NMFKLError(st, "submit")
+        return Ticket(t.value, kind, (F, W, sweeps, obj), F, W, sweeps[:V.m] if kind == 0 else sweeps,
+                      obj[:V.m] if kind == 0 else obj)
+
+    def submit_foldin(self, V, rel_tol: float = 1e-5, max_sweeps: int = 100) -> Ticket:
+        """F for the documents (columns) of V (n x m, the model's n) under W."""
+        return self._submit(0, V, self.r, 0, rel_tol, max_sweeps)
+
+    def submit_fit(self, V, r: int, seed: int = 0, rel_tol: float = 1e-4, max_sweeps: int = 50) -> Ticket:
+        """A full factorization of V with r factors from a Uniform[0,1) start."""
+        return self._submit(1, V, int(r), int(seed), rel_tol, max_sweeps)
+
+    def poll(self, t: Ticket) -> bool:
+        res = _native.Result()
+        st = self._lib.nmfkl_server_poll(self._h, t.id, ctypes.byref(res))
+        if st == 6:
+            return False
+        if st != 0:
+            raise NMFKLError(st, "poll")
+        t._set(res)
+        return True
+
+    def wait(self, t: Ticket) -> Ticket:
+        res = _native.Result()
+        st = self._lib.nmfkl_server_wait(self._h, t.id, ctypes.byref(res))
+        if st != 0:
+            raise NMFKLError(st, "wait")
+        t._set(res)
+        return t
+
+    def stats(self) -> dict:
+        x = _native.ServerStats()
+        self._lib.nmfkl_server_stats(self._h, ctypes.byref(x))
+        return {k: int(getattr(x, k)) for k, _ in _native.ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.nmfkl_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

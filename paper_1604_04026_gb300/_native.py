@@ -20,7 +20,7 @@ class Params(ctypes.Structure):
     _fields_ = [("r", c_i32), ("alpha_W", c_f64), ("beta_W", c_f64), ("alpha_F", c_f64),
                 ("beta_F", c_f64), ("eps_grad", c_f64), ("eps_div", c_f64), ("eps_x", c_f64),
                 ("max_inner", c_i32), ("grad_mode", c_i32), ("break_mode", c_i32),
-                ("perm_mode", c_i32), ("seed", c_u64)]
+                ("perm_mode", c_i32), ("seed", c_u64), ("list_mode", c_i32)]
 
 
 class Counters(ctypes.Structure):
@@ -30,6 +30,26 @@ class Counters(ctypes.Structure):
 class BucketInfo(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_char_p), ("side", c_i32), ("count", c_i32), ("nnz", c_i64),
                 ("max_len", c_i64), ("grid", c_i32), ("block", c_i32), ("smem", c_i64)]
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("device", c_i32), ("slots", c_i32), ("mem_budget", c_i64), ("max_pending", c_i32),
+                ("max_batch_docs", c_i32), ("max_batch_nnz", c_i64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("n", c_i64), ("m", c_i64), ("nnz", c_i64), ("colptr", c_vp), ("rowidx", c_vp),
+                ("val", c_vp), ("r", c_i32), ("seed", c_u64), ("rel_tol", c_f64), ("max_sweeps", c_i32),
+                ("F_out", c_vp), ("W_out", c_vp), ("sweeps_out", c_vp), ("obj_out", c_vp)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", c_i32), ("queued_ms", c_f64), ("run_ms", c_f64), ("batch_requests", c_i32),
+                ("message", ctypes.c_char * 160)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("pending", c_i64), ("mem_in_use", c_i64), ("batches", c_i64), ("batched_requests", c_i64)]
 
 
 # (name, restype, argtypes) of every exported entry point
@@ -55,6 +75,14 @@ SIGNATURES = [
     ("nmfkl_set_timing", c_i32, [c_vp, c_i32]),
     ("nmfkl_kernel_times", c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32]),
     ("nmfkl_debug_perm", c_i32, [c_vp, c_i64, c_i32, c_i64, c_vp, c_vp]),
+    ("nmfkl_server_default_cfg", None, [ctypes.POINTER(ServerCfg)]),
+    ("nmfkl_server_create", c_i32, [ctypes.POINTER(ServerCfg), ctypes.POINTER(Params), c_i64, c_vp,
+                                    ctypes.POINTER(c_vp)]),
+    ("nmfkl_server_submit", c_i32, [c_vp, ctypes.POINTER(Request), ctypes.POINTER(c_u64)]),
+    ("nmfkl_server_poll", c_i32, [c_vp, c_u64, ctypes.POINTER(Result)]),
+    ("nmfkl_server_wait", c_i32, [c_vp, c_u64, ctypes.POINTER(Result)]),
+    ("nmfkl_server_stats", c_i32, [c_vp, ctypes.POINTER(ServerStats)]),
+    ("nmfkl_server_destroy", None, [c_vp]),
     ("nmfkl_sweep_F_noalloc", c_i32, [ctypes.POINTER(Params), c_i64, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp,
                                       c_vp, c_i64, c_vp]),
 ]

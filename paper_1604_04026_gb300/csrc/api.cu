@@ -157,7 +157,8 @@ nmfkl_status nmfkl_create(const nmfkl_params *p, int64_t n, int64_t m, int32_t d
     *out = nullptr;
     if (!p || p->r < 1 || p->r > kMaxR || n < 1 || m < 1 || n > INT32_MAX || m > INT32_MAX ||
         !(p->eps_x >= 0) || p->max_inner < 0 || !(p->eps_div >= 0) || !(p->eps_grad >= 0) ||
-        p->alpha_W < 0 || p->alpha_F < 0 || p->beta_W < 0 || p->beta_F < 0)
+        p->alpha_W < 0 || p->alpha_F < 0 || p->beta_W < 0 || p->beta_F < 0 || p->list_mode < 0 ||
+        p->list_mode > 2)
         return NMFKL_EINVAL;
     nmfkl_ctx *c = new (std::nothrow) nmfkl_ctx();
     if (!c) return NMFKL_ENOMEM;
@@ -168,7 +169,8 @@ nmfkl_status nmfkl_create(const nmfkl_params *p, int64_t n, int64_t m, int32_t d
     c->device = device;
     c->stream = (cudaStream_t)stream;
     if (!cuda_ok(c, cudaSetDevice(device), "cudaSetDevice") ||
-        !cuda_ok(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count")) {
+        !cuda_ok(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count") ||
+        !cuda_ok(c, kernel_attributes(device), "kernel attributes")) {
         delete c;
         return NMFKL_ECUDA;
     }
@@ -178,7 +180,8 @@ nmfkl_status nmfkl_create(const nmfkl_params *p, int64_t n, int64_t m, int32_t d
               dev_alloc(c, &c->dpart, c->dpart_len, "partials") && dev_alloc(c, &c->dscalar, 8, "scalars") &&
               dev_alloc(c, &c->counters, 8, "counters") && dev_alloc(c, &c->queues, 64, "queues") &&
               dev_alloc(c, &c->err_flag, 1, "error flag") && dev_alloc(c, &c->dsum[0], c->ldr, "sumW64") &&
-              dev_alloc(c, &c->dsum[1], c->ldr, "sumF64") && dev_alloc(c, &c->unit_obj, n, "row objective");
+              dev_alloc(c, &c->dsum[1], c->ldr, "sumF64") && dev_alloc(c, &c->unit_obj, n, "row objective") &&
+              dev_alloc(c, &c->dens, 1, "density");
     if (!ok) {
         nmfkl_destroy(c);
         return NMFKL_ENOMEM;
@@ -203,7 +206,7 @@ void nmfkl_destroy(nmfkl_ctx *c) {
     cudaFree(c->Wt); cudaFree(c->Ft); cudaFree(c->sumW); cudaFree(c->sumF); cudaFree(c->dpart);
     cudaFree(c->dscalar); cudaFree(c->counters); cudaFree(c->queues); cudaFree(c->err_flag);
     cudaFree(c->tbuf);
-    cudaFree(c->dsum[0]); cudaFree(c->dsum[1]); cudaFree(c->unit_obj);
+    cudaFree(c->dsum[0]); cudaFree(c->dsum[1]); cudaFree(c->unit_obj); cudaFree(c->dens);
     for (auto &pd : c->pending) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -472,10 +475,18 @@ static nmfkl_status fold_reserve(nmfkl_ctx *c, int64_t m_new, int64_t nnz) {
     return NMFKL_OK;
 }
 
-nmfkl_status nmfkl_foldin(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_t *colptr, const int32_t *rowidx,
-                          const float *val, const int64_t *doc_ids, const float *F0, float *F_out, double rel_tol,
-                          int32_t max_sweeps, int32_t *sweeps_done, double *doc_obj, int32_t launch_mode,
-                          int32_t mem_kind) {
+}  // extern "C"
+
+namespace nmfkl {
+
+// nmfkl_foldin; with `segs`, the starting F is drawn per segment of columns
+// (each from Uniform[0,1) as if the segment were a batch of its own, or
+// copied from the segment's host F0), so that a segment's result does not
+// depend on the batch it shares (the serving loop merges requests this way).
+nmfkl_status foldin_impl(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_t *colptr, const int32_t *rowidx,
+                         const float *val, const int64_t *doc_ids, const float *F0,
+                         const std::vector<FoldSegment> *segs, float *F_out, double rel_tol, int32_t max_sweeps,
+                         int32_t *sweeps_done, double *doc_obj, int32_t launch_mode, int32_t mem_kind) {
     if (!c) return NMFKL_EINVAL;
     if (m_new < 0 || m_new > INT32_MAX || nnz < 0 || !colptr || (nnz > 0 && (!rowidx || !val)) || !F_out ||
         !(rel_tol >= 0) || max_sweeps < 0 || launch_mode < 0 || launch_mode > 2 || (mem_kind != 0 && mem_kind != 1)) {
@@ -520,7 +531,28 @@ nmfkl_status nmfkl_foldin(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_
         }
     }
     // starting F, unit-major
-    if (m_new > 0) {
+    if (segs) {
+        for (const FoldSegment &g : *segs) {
+            if (g.m <= 0) continue;
+            if (!g.F0) {
+                uniform_init_raw(c->stream, f.Ft + g.col0 * c->ldr, c->p.r, g.m, c->ldr, c->p.seed, 2);
+                continue;
+            }
+            if (c->tbuf_floats < r * g.m) {
+                cudaFree(c->tbuf);
+                c->tbuf = nullptr;
+                c->tbuf_floats = 0;
+                if (!dev_alloc(c, &c->tbuf, r * g.m, "transpose buffer")) return NMFKL_ENOMEM;
+                c->tbuf_floats = r * g.m;
+            }
+            if (!cuda_ok(c, cudaMemcpyAsync(c->tbuf, g.F0, sizeof(float) * r * g.m, cudaMemcpyHostToDevice, c->stream),
+                         "copy segment F0"))
+                return NMFKL_ECUDA;
+            st = launch_to_unit_major(c, c->tbuf, f.Ft + g.col0 * c->ldr, g.m);
+            if (st != NMFKL_OK) return st;
+            if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "segment F0 sync")) return NMFKL_ECUDA;
+        }
+    } else if (m_new > 0) {
         if (!F0) {
             uniform_init_raw(c->stream, f.Ft, c->p.r, m_new, c->ldr, c->p.seed, 2);
         } else {
@@ -561,13 +593,26 @@ nmfkl_status nmfkl_foldin(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_
     return NMFKL_OK;
 }
 
+}  // namespace nmfkl
+
+extern "C" {
+
+nmfkl_status nmfkl_foldin(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_t *colptr, const int32_t *rowidx,
+                          const float *val, const int64_t *doc_ids, const float *F0, float *F_out, double rel_tol,
+                          int32_t max_sweeps, int32_t *sweeps_done, double *doc_obj, int32_t launch_mode,
+                          int32_t mem_kind) {
+    return foldin_impl(c, m_new, nnz, colptr, rowidx, val, doc_ids, F0, nullptr, F_out, rel_tol, max_sweeps,
+                       sweeps_done, doc_obj, launch_mode, mem_kind);
+}
+
 int32_t nmfkl_plan_info(const nmfkl_ctx *c, nmfkl_bucket_info *out, int32_t cap) {
     if (!c) return -1;
     int32_t i = 0;
     for (int side = 0; side < 2; ++side)
-        for (const auto &b : c->plan[side]) {
+        for (const auto *pl : {&c->plan[side], &c->plan_sparse[side]})
+        for (const auto &b : *pl) {
             if (out && i < cap) {
-                out[i].kernel = kind_name(b.kind);
+                out[i].kernel = bucket_name(b);
                 out[i].side = side;
                 out[i].count = b.count;
                 out[i].nnz = b.nnz;

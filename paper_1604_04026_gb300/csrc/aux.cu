@@ -330,6 +330,29 @@ void launch_from_unit_major_raw(cudaStream_t st, const float *src, float *dst, i
     from_unit_major_kernel<<<grid, dim3(32, 8), 0, st>>>(src, dst, r, cols, ldr);
 }
 
+__global__ void density_kernel(const float *At, int64_t rows, int ldr, int r, const int64_t *ptr,
+                               unsigned long long *out) {
+    // one warp per row: lanes read the row's coordinates, a ballot counts the positive ones
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < rows; i += warps) {
+        const float *row = At + i * ldr;
+        unsigned c = 0;
+        for (int k0 = 0; k0 < r; k0 += 32) {
+            const int k = k0 + lane;
+            c += __popc(__ballot_sync(0xffffffffu, k < r && row[k] > 0.f));
+        }
+        acc += (unsigned long long)c * (unsigned long long)(ptr[i + 1] - ptr[i]);
+    }
+    if (lane == 0 && acc) atomicAdd(out, acc);
+}
+
+void launch_density(cudaStream_t st, const float *At, int64_t rows, int ldr, int r, const int64_t *ptr,
+                    unsigned long long *out) {
+    density_kernel<<<1024, 256, 0, st>>>(At, rows, ldr, r, ptr, out);
+}
+
 nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, const int64_t *ptr,
                              const int32_t *idx, const float *val, int32_t *flag) {
     validate_kernel<<<256, 256, 0, c->stream>>>(units, extent, ptr, idx, val, flag);

@@ -93,6 +93,7 @@ struct HalfArgs {
 
 // One launch configuration of the sweep kernel family.
 struct Bucket {
+    bool sparse = false;  // kernel table: the sparse-list kinds (else the dense-tile kinds)
     int kind;         // index into the kernel table
     int nt;           // threads per subproblem group (32 = one warp)
     int k;            // nonzeros per thread held in registers (0 = giant)
@@ -174,7 +175,11 @@ struct nmfkl_ctx {
     int64_t scratch_floats = 0;
     float *tbuf = nullptr;         // transpose staging for get/set
     int64_t tbuf_floats = 0;
-    std::vector<nmfkl::Bucket> plan[2];
+    std::vector<nmfkl::Bucket> plan[2];         // dense-tile kernels
+    std::vector<nmfkl::Bucket> plan_sparse[2];  // sparse-list kernels
+    unsigned long long *dens = nullptr;         // density numerators of the two halves
+    double density[2] = {-1.0, -1.0};           // last measured density per half
+    int used_sparse[2] = {-1, -1};              // which plan the last half ran
     nmfkl::FoldState *fold = nullptr;
     // timing
     bool timing = false;
@@ -194,10 +199,14 @@ int timer_begin(nmfkl_ctx *c, const char *name);
 void timer_end(nmfkl_ctx *c, int token);
 
 // sweep.cu
+// Gives every kernel the device's opt-in dynamic shared memory limit (once per
+// device; the limit is process-wide per-function state).
+cudaError_t kernel_attributes(int device);
 nmfkl_status plan_side(nmfkl_ctx *c, int side);
 nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep);
 void free_plan(nmfkl_ctx *c);
 const char *kind_name(int kind);
+const char *bucket_name(const Bucket &b);
 
 // aux.cu
 nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out, double *out_d);
@@ -218,8 +227,21 @@ int64_t dpart_required(int ldr);
 nmfkl_status foldin_run(nmfkl_ctx *c, int64_t m_new, bool with_ids, double rel_tol, int32_t max_sweeps,
                         bool use_graph);
 nmfkl_status foldin_per_doc(nmfkl_ctx *c, int64_t m_new, double rel_tol, int32_t max_sweeps);
+// api.cu: fold-in with the starting F given per segment of columns (serving)
+struct FoldSegment {
+    int64_t col0, m;
+    const float *F0;  // host r x m row-major, or NULL: Uniform[0,1) drawn for the segment alone
+};
+nmfkl_status foldin_impl(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_t *colptr, const int32_t *rowidx,
+                         const float *val, const int64_t *doc_ids, const float *F0,
+                         const std::vector<FoldSegment> *segs, float *F_out, double rel_tol, int32_t max_sweeps,
+                         int32_t *sweeps_done, double *doc_obj, int32_t launch_mode, int32_t mem_kind);
 int foldin_kind_for_length(int64_t L);
 void free_fold(nmfkl_ctx *c);
+// Sum over the rows i of At of weight_i * #{k < r : At[i][k] > 0}, weight_i =
+// ptr[i+1] - ptr[i], into *out (zeroed by the caller).
+void launch_density(cudaStream_t st, const float *At, int64_t rows, int ldr, int r, const int64_t *ptr,
+                    unsigned long long *out);
 nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, const int64_t *ptr,
                              const int32_t *idx, const float *val, int32_t *flag);
 

@@ -974,6 +974,336 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Sparse-list groups. A nonzero p with A_pk = 0 adds nothing to either sum of
+// Eq. Partial for coordinate k and its x_p does not move when x_k does, so
+// coordinate k only needs the nonzeros with A_pk > 0 (the paper's use of the
+// sparsity of W and F, Section 2). Staging writes, per warp of the group and
+// per k, the list of (p, A_pk) over that warp's nonzeros with A_pk > 0, in
+// increasing p (one ballot per k per 32 nonzeros), into the group's scratch
+// slot; the coordinate loop then visits only those entries. The per-nonzero
+// state (x_p, v_p), (w_p, q_p) and the positive-term count is addressed by p:
+// in shared memory, or for giant units in the scratch slot.
+// Warp w of the group owns the chunks of 32 nonzeros c = w, w + NW, ...; its
+// lists hold only its own nonzeros, so warps never touch each other's state.
+// ---------------------------------------------------------------------------
+constexpr int kSparseE = 4;  // list entries per lane prefetched into registers
+
+struct SparseLayout {
+    size_t words_off, cnt_off, red_off, xv_off, wq_off, tm_off, bytes;
+};
+// scap: nonzeros whose state is in shared memory (0: state in the slot)
+__host__ __device__ inline SparseLayout sparse_layout(int r, int ldr, int nt, int scap) {
+    SparseLayout g{};
+    size_t off = align16(256 + 2 * (size_t)ldr * 4);  // perm | x_init | x_out
+    g.words_off = off;
+    off = align16(off + 8 * (size_t)(r > 1 ? r - 1 : 1));
+    g.cnt_off = off;
+    off = align16(off + 4 * (size_t)(nt / 32) * ldr);
+    g.red_off = off;
+    off = align16(off + 2 * (size_t)(nt / 32) * sizeof(float2));
+    g.xv_off = off;
+    off = align16(off + 8 * (size_t)scap);
+    g.wq_off = off;
+    off = align16(off + 8 * (size_t)scap);
+    g.tm_off = off;
+    off = align16(off + 2 * (size_t)scap);
+    g.bytes = off;
+    return g;
+}
+// Scratch slot of a sparse group (floats): lists [NW][r][lcap/NW] of int2,
+// then, for giant units, the state xv[lcap], wq[lcap] (float2) and tm[lcap].
+__host__ __device__ inline int64_t sparse_slot_floats(int r, int lcap, bool smem_state) {
+    int64_t f = 2 * (int64_t)r * lcap;
+    if (!smem_state) f += 4 * (int64_t)lcap + (lcap + 1) / 2;
+    return (f + 63) / 64 * 64;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <int NT>
+__host__ __device__ constexpr int sparse_min_blocks() {
+    return NT == 32 ? 3 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
+}
+template <int NT, bool kSmemState>
+__global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) sparse_kernel(HalfArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool kCta = NT > 32;
+    constexpr int kNW = NT / 32;
+    constexpr int E = kSparseE;
+    const int lane = threadIdx.x & 31;
+    const int warp_in_block = threadIdx.x >> 5;
+    const int group_in_block = kCta ? 0 : warp_in_block;
+    const int groups_per_block = kCta ? 1 : (int)(blockDim.x >> 5);
+    const int w = kCta ? warp_in_block : 0;
+    const int tid_g = kCta ? (int)threadIdx.x : lane;
+    const int group_global = blockIdx.x * groups_per_block + group_in_block;
+
+    const int r = a.r, ldr = a.ldr, lcap = a.lcap, nf4 = ldr >> 2;
+    const int LW = lcap / kNW;
+    const SparseLayout lay = sparse_layout(r, ldr, NT, kSmemState ? lcap : 0);
+    unsigned char *gs = smem_raw + (size_t)group_in_block * lay.bytes;
+    uint8_t *perm = gs;
+    float *x_init = reinterpret_cast<float *>(gs + 256);
+    float *x_out = x_init + ldr;
+    uint64_t *words = reinterpret_cast<uint64_t *>(gs + lay.words_off);
+    int *mycnt = reinterpret_cast<int *>(gs + lay.cnt_off) + w * ldr;
+    float2 *red = reinterpret_cast<float2 *>(gs + lay.red_off);
+    float *slot = a.scratch + (int64_t)group_global * a.slot_floats;
+    int2 *mylists = reinterpret_cast<int2 *>(slot) + (int64_t)w * r * LW;
+    float2 *xv, *wq;
+    uint16_t *tm;
+    if constexpr (kSmemState) {
+        xv = reinterpret_cast<float2 *>(gs + lay.xv_off);
+        wq = reinterpret_cast<float2 *>(gs + lay.wq_off);
+        tm = reinterpret_cast<uint16_t *>(gs + lay.tm_off);
+    } else {
+        xv = reinterpret_cast<float2 *>(slot + 2 * (int64_t)r * lcap);
+        wq = xv + lcap;
+        tm = reinterpret_cast<uint16_t *>(wq + lcap);
+    }
+    __shared__ int s_q;
+    const float eps_div = a.eps_div;
+    const int count = a.count_dev ? *a.count_dev : a.count;
+    Tally tally;
+    int parity = 0;
+
+    auto group_sync = [&]() {
+        if constexpr (kCta) __syncthreads(); else __syncwarp();
+    };
+    auto reduce = [&](float sg, float sh) -> float2 {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sg += __shfl_xor_sync(kFull, sg, o);
+            sh += __shfl_xor_sync(kFull, sh, o);
+        }
+        if constexpr (kCta) {
+            float2 *rb = red + parity * kNW;
+            if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
+            __syncthreads();
+            float tg = 0.f, th = 0.f;
+#pragma unroll
+            for (int i = 0; i < kNW; ++i) {
+                const float2 v = rb[i];
+                tg += v.x;
+                th += v.y;
+            }
+            parity ^= 1;
+            return make_float2(tg, th);
+        } else {
+            return make_float2(sg, sh);
+        }
+    };
+
+    for (;;) {
+        int qi;
+        if constexpr (kCta) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_q = atomicAdd(a.queue, 1);
+            __syncthreads();
+            qi = s_q;
+        } else {
+            __syncwarp();
+            int q = 0;
+            if (lane == 0) q = atomicAdd(a.queue, 1);
+            qi = __shfl_sync(kFull, q, 0);
+        }
+        if (qi >= count) break;
+        const int64_t u = a.units[qi];
+        const int64_t base = a.ptr[u];
+        const int L = (int)(a.ptr[u + 1] - base);
+        const int64_t perm_unit = a.unit_ids ? a.unit_ids[u] : u;
+        if (L > lcap) {  // cannot happen with a consistent plan; refuse rather than overrun
+            if (tid_g == 0) atomicOr(a.err, 4);
+            continue;
+        }
+        for (int k = tid_g; k < ldr; k += NT) {
+            const float xk = a.X[u * ldr + k];
+            x_init[k] = xk;
+            x_out[k] = xk;
+        }
+        for (int k = lane; k < ldr; k += 32) mycnt[k] = 0;
+        group_sync();
+
+        // ---- stage: x_p, the state, and this warp's lists
+        const int nchunks = (L + 31) >> 5;
+        const float4 *x4 = reinterpret_cast<const float4 *>(x_init);
+        int4 *cnt4 = reinterpret_cast<int4 *>(mycnt);
+        const unsigned lt = lanemask_lt();
+        for (int c = w; c < nchunks; c += kNW) {
+            const int p = 32 * c + lane;
+            const bool valid = p < L;
+            int idx = 0;
+            float v = 0.f;
+            if (valid) {
+                idx = a.idx[base + p];
+                v = a.val[base + p];
+            }
+            const float4 *row = reinterpret_cast<const float4 *>(a.At + (int64_t)idx * ldr);
+            float acc = 0.f;
+            int terms = 0;
+            constexpr int kB = 4;
+            for (int f0 = 0; f0 < nf4; f0 += kB) {
+                float4 buf[kB];
+#pragma unroll
+                for (int b = 0; b < kB; ++b)
+                    buf[b] = (valid && f0 + b < nf4) ? __ldg(row + f0 + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < kB; ++b) {
+                    const int f = f0 + b;
+                    if (f < nf4) {
+                        const float4 av = buf[b];
+                        const float4 xk = x4[f];
+                        const int4 c4 = cnt4[f];
+                        acc = fmaf(av.x, xk.x, acc);
+                        acc = fmaf(av.y, xk.y, acc);
+                        acc = fmaf(av.z, xk.z, acc);
+                        acc = fmaf(av.w, xk.w, acc);
+                        terms += (av.x > 0.f && xk.x > 0.f) + (av.y > 0.f && xk.y > 0.f) +
+                                 (av.z > 0.f && xk.z > 0.f) + (av.w > 0.f && xk.w > 0.f);
+                        // padding columns (k >= r) hold 0 and never enter a list
+                        const unsigned m0 = __ballot_sync(kFull, av.x > 0.f);
+                        const unsigned m1 = __ballot_sync(kFull, av.y > 0.f);
+                        const unsigned m2 = __ballot_sync(kFull, av.z > 0.f);
+                        const unsigned m3 = __ballot_sync(kFull, av.w > 0.f);
+                        int2 *l0 = mylists + (int64_t)(4 * f) * LW;
+                        if (av.x > 0.f) l0[c4.x + __popc(m0 & lt)] = make_int2(p, __float_as_int(av.x));
+                        if (av.y > 0.f) l0[LW + c4.y + __popc(m1 & lt)] = make_int2(p, __float_as_int(av.y));
+                        if (av.z > 0.f) l0[2 * LW + c4.z + __popc(m2 & lt)] = make_int2(p, __float_as_int(av.z));
+                        if (av.w > 0.f) l0[3 * LW + c4.w + __popc(m3 & lt)] = make_int2(p, __float_as_int(av.w));
+                        if (lane == 0)
+                            cnt4[f] = make_int4(c4.x + __popc(m0), c4.y + __popc(m1), c4.z + __popc(m2),
+                                                c4.w + __popc(m3));
+                    }
+                }
+            }
+            if (valid) {
+                const float xl = terms == 0 ? 0.f : acc;
+                const float ri = recip(xl + eps_div);
+                xv[p] = make_float2(xl, v);
+                wq[p] = make_float2(v * ri, v * ri * ri);
+                tm[p] = (uint16_t)terms;
+            }
+            __syncwarp();
+        }
+        if (w == 0) {
+            ids_words_warp(words, r, perm_unit, a.sweep, a.side, a.perm_mode, a.seed, lane);
+            __syncwarp();
+            if (lane == 0) fisher_yates(perm, words, r);
+            __syncwarp();
+        }
+        group_sync();
+
+        // ---- Algorithm 2 over this unit's coordinates, list entries only
+        int2 cur[E], nxt[E];
+        int ccur = 0, cnxt = 0;
+        auto fetch = [&](int pos, int2 (&dst)[E], int &cn) {
+            cn = 0;
+            if (pos < r) {
+                const int k = perm[pos];
+                cn = mycnt[k];
+                const int2 *lk = mylists + (int64_t)k * LW;
+#pragma unroll
+                for (int t = 0; t < E; ++t) {
+                    const int j = lane + 32 * t;
+                    dst[t] = j < cn ? __ldcg(lk + j) : make_int2(0, 0);
+                }
+            }
+        };
+        fetch(0, cur, ccur);
+        for (int kk = 0; kk < r; ++kk) {
+            const int k = perm[kk];
+            fetch(kk + 1, nxt, cnxt);
+            const int2 *lk = mylists + (int64_t)k * LW;
+            const int cn = ccur;
+            auto eval = [&]() -> float2 {
+                float sg = 0.f, sh = 0.f;
+#pragma unroll
+                for (int t = 0; t < E; ++t) {
+                    if (lane + 32 * t < cn) {
+                        const float av = __int_as_float(cur[t].y);
+                        const float2 s = wq[cur[t].x];
+                        sg = fmaf(s.x, av, sg);
+                        sh = fmaf(s.y * av, av, sh);
+                    }
+                }
+                for (int j = lane + 32 * E; j < cn; j += 32) {
+                    const int2 e = __ldcg(lk + j);
+                    const float av = __int_as_float(e.y);
+                    const float2 s = wq[e.x];
+                    sg = fmaf(s.x, av, sg);
+                    sh = fmaf(s.y * av, av, sh);
+                }
+                return reduce(sg, sh);
+            };
+            auto update_one = [&](int p, float av, float d, int dc) {
+                const float2 s = xv[p];
+                int terms = dc != 0 ? (int)tm[p] : 0;
+                const float xn = step_x(s.x, av, d, dc, terms);
+                if (dc != 0) tm[p] = (uint16_t)terms;
+                const float ri = recip(xn + eps_div);
+                xv[p].x = xn;
+                wq[p] = make_float2(s.y * ri, s.y * ri * ri);
+            };
+            auto update = [&](float d, int dc) {
+#pragma unroll
+                for (int t = 0; t < E; ++t)
+                    if (lane + 32 * t < cn) update_one(cur[t].x, __int_as_float(cur[t].y), d, dc);
+                for (int j = lane + 32 * E; j < cn; j += 32) {
+                    const int2 e = __ldcg(lk + j);
+                    update_one(e.x, __int_as_float(e.y), d, dc);
+                }
+                // the next evaluation may read these entries from other lanes
+                __syncwarp();
+            };
+            const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+            if (tid_g == 0) x_out[k] = xk;
+#pragma unroll
+            for (int t = 0; t < E; ++t) cur[t] = nxt[t];
+            ccur = cnxt;
+        }
+        if (a.unit_obj) {
+            float t = 0.f;
+            for (int c = w; c < nchunks; c += kNW) {
+                const int p = 32 * c + lane;
+                if (p < L) {
+                    const float2 s = xv[p];
+                    t += kl_term(s.y, s.x, eps_div);
+                }
+            }
+            double dt = warp_sum_d((double)t);
+            if constexpr (kCta) {
+                double *rd = reinterpret_cast<double *>(red + parity * kNW);
+                if (lane == 0) rd[warp_in_block] = dt;
+                __syncthreads();
+                double tot = 0.0;
+#pragma unroll
+                for (int i = 0; i < kNW; ++i) tot += rd[i];
+                parity ^= 1;
+                dt = tot;
+            }
+            if (tid_g == 0) a.unit_obj[u] = dt;
+        }
+        group_sync();
+        // drop this warp's finished list lines from L2 (whole lines only)
+        for (int k = 0; k < r; ++k) {
+            const int lines = (mycnt[k] * 8) / 128;
+            const char *l0 = reinterpret_cast<const char *>(mylists + (int64_t)k * LW);
+            for (int i = lane; i < lines; i += 32) asm volatile("discard.global.L2 [%0], 128;" ::"l"(l0 + 128 * i) : "memory");
+        }
+        for (int k = tid_g; k < r; k += NT) {
+            const float xk = x_out[k];
+            if (!(xk == xk)) atomicOr(a.err, 1);
+            a.X[u * ldr + k] = xk;
+        }
+    }
+    if (tid_g == 0) flush_tally(a, tally);
+}
+
+// ---------------------------------------------------------------------------
 // Host side: the bucket table and the plan.
 // ---------------------------------------------------------------------------
 struct KernelKind {
@@ -1018,8 +1348,6 @@ size_t cluster_smem_bytes(int r, int ldr) {
 // Clusters of `cl` CTAs of the cluster kernel that fit on the device at once.
 int active_clusters(int cl, size_t smem) {
     const void *fn = kKinds[kGiantKind - 1].fn;
-    if (cl > 8) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(cl);
     cfg.blockDim = dim3(kClusterNT);
@@ -1039,17 +1367,114 @@ int active_clusters(int cl, size_t smem) {
     return n;
 }
 
+struct SparseKind {
+    const void *fn;
+    int nt;      // threads per group (32: warp groups, several per block)
+    int cap;     // longest unit (nonzeros) of the class; 0: no limit (state in the slot)
+    const char *name;
+};
+const SparseKind kSparseKinds[] = {
+    {(const void *)sparse_kernel<32, true>, 32, 512, "sparse_warp"},
+    {(const void *)sparse_kernel<128, true>, 128, 1024, "sparse_cta128"},
+    {(const void *)sparse_kernel<256, true>, 256, 2048, "sparse_cta256"},
+    {(const void *)sparse_kernel<512, true>, 512, 8192, "sparse_cta512"},
+    {(const void *)sparse_kernel<1024, false>, 1024, 0, "sparse_giant"},
+};
+constexpr int kNumSparseKinds = sizeof(kSparseKinds) / sizeof(kSparseKinds[0]);
+
+int sparse_kind_for_length(int64_t L) {
+    for (int i = 0; i < kNumSparseKinds - 1; ++i)
+        if (L <= kSparseKinds[i].cap) return i;
+    return kNumSparseKinds - 1;
+}
+
 }  // namespace
 
 const char *kind_name(int kind) { return kKinds[kind].name; }
+const char *bucket_name(const Bucket &b) { return b.sparse ? kSparseKinds[b.kind].name : kKinds[b.kind].name; }
+
+
 
 void free_plan(nmfkl_ctx *c) {
     for (int side = 0; side < 2; ++side) {
-        for (auto &b : c->plan[side])
-            if (b.d_units) cudaFree(b.d_units);
-        c->plan[side].clear();
+        for (auto *pl : {&c->plan[side], &c->plan_sparse[side]}) {
+            for (auto &b : *pl)
+                if (b.d_units) cudaFree(b.d_units);
+            pl->clear();
+        }
     }
 }
+
+namespace {
+
+// Sparse-list plan of one half: one bucket per length class; a class's tile
+// row length is its longest unit rounded up to whole chunks of every warp.
+nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t> &ptr, int optin) {
+    const int64_t units = (int64_t)ptr.size() - 1;
+    const int r = c->p.r, ldr = c->ldr;
+    std::vector<std::vector<int32_t>> lists(kNumSparseKinds);
+    std::vector<int64_t> maxlen(kNumSparseKinds, 0), nnz(kNumSparseKinds, 0);
+    for (int64_t u = 0; u < units; ++u) {
+        const int64_t L = ptr[u + 1] - ptr[u];
+        const int kind = sparse_kind_for_length(L);
+        lists[kind].push_back((int32_t)u);
+        maxlen[kind] = std::max(maxlen[kind], L);
+        nnz[kind] += L;
+    }
+    for (int kind = 0; kind < kNumSparseKinds; ++kind) {
+        auto &lst = lists[kind];
+        if (lst.empty()) continue;
+        std::stable_sort(lst.begin(), lst.end(), [&](int32_t x, int32_t y) {
+            return (ptr[x + 1] - ptr[x]) > (ptr[y + 1] - ptr[y]);
+        });
+        const SparseKind &sk = kSparseKinds[kind];
+        const bool smem_state = sk.cap > 0;
+        const bool cta = sk.nt > 32;
+        Bucket b{};
+        b.sparse = true;
+        b.kind = kind;
+        b.nt = sk.nt;
+        b.k = 0;
+        b.cl = 1;
+        b.count = (int32_t)lst.size();
+        b.max_len = maxlen[kind];
+        b.nnz = nnz[kind];
+        const int64_t chunk = 32 * (int64_t)(sk.nt / 32);
+        b.lcap = (int32_t)std::max<int64_t>(chunk, (b.max_len + chunk - 1) / chunk * chunk);
+        const size_t gbytes = sparse_layout(r, ldr, sk.nt, smem_state ? b.lcap : 0).bytes;
+        int gpb = 1;
+        if (!cta) {
+            gpb = 8;
+            while (gpb > 1 && gbytes * gpb > (size_t)optin) --gpb;
+        }
+        b.block = cta ? sk.nt : 32 * gpb;
+        b.smem = gbytes * gpb;
+        if (b.smem > (size_t)optin) {
+            c->err = "sparse plan: shared memory exceeds the device limit";
+            return NMFKL_EINVAL;
+        }
+        int per_sm = 0;
+        if (!cuda_ok(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sk.fn, b.block, b.smem), "occupancy"))
+            return NMFKL_ECUDA;
+        if (per_sm < 1) {
+            c->err = std::string("kernel ") + sk.name + " cannot be resident";
+            return NMFKL_EINVAL;
+        }
+        const int64_t need_blocks = (b.count + gpb - 1) / gpb;
+        b.grid = (int)std::min<int64_t>(need_blocks, (int64_t)per_sm * c->num_sms);
+        b.groups = b.grid * gpb;
+        b.slot_floats = sparse_slot_floats(r, b.lcap, smem_state);
+        if (!cuda_ok(c, cudaMalloc(&b.d_units, sizeof(int32_t) * lst.size()), "alloc unit list")) return NMFKL_ENOMEM;
+        if (!cuda_ok(c, cudaMemcpy(b.d_units, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice),
+                     "copy unit list"))
+            return NMFKL_ECUDA;
+        c->plan_sparse[side].push_back(b);
+        c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
+    }
+    return NMFKL_OK;
+}
+
+}  // namespace
 
 nmfkl_status plan_side(nmfkl_ctx *c, int side) {
     const int64_t units = side == 0 ? c->m : c->n;
@@ -1125,10 +1550,6 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
             c->err = "shared memory plan exceeds the device limit";
             return NMFKL_EINVAL;
         }
-        if (!cuda_ok(c, cudaFuncSetAttribute(kKinds[kind].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)b.smem),
-                     "set smem attribute"))
-            return NMFKL_ECUDA;
         int per_sm = 0;
         if (!cuda_ok(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kKinds[kind].fn, b.block, b.smem),
                      "occupancy"))
@@ -1157,7 +1578,7 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
         c->plan[side].push_back(b);
         c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
     }
-    return NMFKL_OK;
+    return plan_side_sparse(c, side, ptr, optin);
 }
 
 nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
@@ -1192,8 +1613,23 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
     a.counters = c->counters;
     a.err = c->err_flag;
     a.unit_obj = F ? nullptr : c->unit_obj;
+    // dense tile or sparse lists (list_mode): in automatic mode, the lists when
+    // the fixed factor is less than half dense at the nonzeros of V
+    bool sparse = c->p.list_mode == 2;
+    if (c->p.list_mode == 0) {
+        unsigned long long h = 0;
+        if (!cuda_ok(c, cudaMemsetAsync(c->dens, 0, sizeof(unsigned long long), c->stream), "density reset"))
+            return NMFKL_ECUDA;
+        launch_density(c->stream, At, F ? c->n : c->m, c->ldr, c->p.r, F ? c->rowptr : c->colptr, c->dens);
+        if (!cuda_ok(c, cudaMemcpyAsync(&h, c->dens, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "density") ||
+            !cuda_ok(c, cudaStreamSynchronize(c->stream), "density sync"))
+            return NMFKL_ECUDA;
+        c->density[side] = c->nnz > 0 ? (double)h / ((double)c->nnz * c->p.r) : 0.0;
+        sparse = c->density[side] < 0.5;
+    }
+    c->used_sparse[side] = sparse ? 1 : 0;
     int qi = 0;
-    for (auto &b : c->plan[side]) {
+    for (auto &b : sparse ? c->plan_sparse[side] : c->plan[side]) {
         a.units = b.d_units;
         a.count = b.count;
         a.queue = c->queues + side * 16 + qi++;
@@ -1202,9 +1638,11 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
         if (!cuda_ok(c, cudaMemsetAsync(a.queue, 0, sizeof(int32_t), c->stream), "reset queue"))
             return NMFKL_ECUDA;
         void *args[] = {&a};
-        const int tok = timer_begin(c, kKinds[b.kind].name);
+        const int tok = timer_begin(c, bucket_name(b));
         cudaError_t e;
-        if (b.cl > 1) {
+        if (b.sparse) {
+            e = cudaLaunchKernel(kSparseKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, c->stream);
+        } else if (b.cl > 1) {
             cudaLaunchConfig_t cfg{};
             cfg.gridDim = dim3(b.grid);
             cfg.blockDim = dim3(b.block);
@@ -1222,7 +1660,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
             e = cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, c->stream);
         }
         timer_end(c, tok);
-        if (!cuda_ok(c, e, kKinds[b.kind].name)) return NMFKL_ECUDA;
+        if (!cuda_ok(c, e, bucket_name(b))) return NMFKL_ECUDA;
     }
     return NMFKL_OK;
 }
@@ -1375,9 +1813,6 @@ nmfkl_status fold_plan(nmfkl_ctx *c) {
             c->err = "fold-in: shared memory plan exceeds the device limit";
             return NMFKL_EINVAL;
         }
-        if (!cuda_ok(c, cudaFuncSetAttribute(kk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem[kind]),
-                     "fold-in smem attribute"))
-            return NMFKL_ECUDA;
         int per_sm = 0;
         if (!cuda_ok(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kk.fn, f.block[kind], f.smem[kind]),
                      "fold-in occupancy"))
@@ -1571,8 +2006,7 @@ extern "C" nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, 
     int gpb = 8;
     while (gpb > 1 && gbytes * gpb > (size_t)optin) --gpb;
     const size_t smem = gbytes * gpb;
-    if (cudaFuncSetAttribute(kk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return NMFKL_ECUDA;
+    if (kernel_attributes(dev) != cudaSuccess) return NMFKL_ECUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kk.fn, 32 * gpb, smem) != cudaSuccess || per_sm < 1)
         return NMFKL_ECUDA;
@@ -1649,6 +2083,44 @@ nmfkl_status launch_debug_perm(nmfkl_ctx *c, int64_t sweep, int side, int64_t co
                                                                           c->p.perm_mode, c->p.seed, out);
     timer_end(c, tok);
     return cuda_ok(c, cudaGetLastError(), "debug_perm") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+namespace {
+// The dynamic shared memory limit and the cluster-size permission are
+// per-function state shared by every context in the process. Contexts that
+// run at once on different streams or host threads (the serving loop) plan
+// different sizes, so each kernel is given the device's opt-in maximum once,
+// instead of each plan setting its own size.
+constexpr int kMaxDevices = 64;
+std::once_flag g_attr_once[kMaxDevices];
+cudaError_t g_attr_err[kMaxDevices];
+
+cudaError_t set_attrs_for(const void *fn, int optin) {
+    // the limit covers dynamic shared memory only; the kernel's static part counts against the block total
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+}  // namespace
+
+cudaError_t kernel_attributes(int device) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(g_attr_once[device], [device] {
+        int optin = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+        for (int i = 0; e == cudaSuccess && i < kNumKinds; ++i) e = set_attrs_for(kKinds[i].fn, optin);
+        for (int i = 0; e == cudaSuccess && i < kFoldKinds; ++i) e = set_attrs_for(kFoldTable[i].fn, optin);
+        for (int i = 0; e == cudaSuccess && i < kNumSparseKinds; ++i) e = set_attrs_for(kSparseKinds[i].fn, optin);
+        for (const KernelKind &kk : kFreeKinds) {
+            if (e != cudaSuccess) break;
+            e = set_attrs_for(kk.fn, optin);
+        }
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kKinds[kGiantKind - 1].fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        g_attr_err[device] = e;
+    });
+    return g_attr_err[device];
 }
 
 }  // namespace nmfkl

@@ -278,3 +278,46 @@ void synth_transpose(int64_t n, int64_t m, const int64_t *colptr, const int32_t 
         }
     free(fill);
 }
+
+/* Poisson means of a masked low-rank count matrix at given entries:
+ * lam[p] = sum_k wtT[rows[p]*r + k] * ftT[cols[p]*r + k] (unit-major factors),
+ * split over `threads` threads by entry range. */
+typedef struct {
+    int64_t p0, p1;
+    int32_t r;
+    const double *wtT, *ftT;
+    const int64_t *rows, *cols;
+    double *lam;
+} lam_job;
+
+static void *lam_worker(void *arg) {
+    lam_job *J = (lam_job *)arg;
+    for (int64_t p = J->p0; p < J->p1; ++p) {
+        const double *a = J->wtT + J->rows[p] * J->r, *b = J->ftT + J->cols[p] * J->r;
+        double s = 0.0;
+        for (int32_t k = 0; k < J->r; ++k) s += a[k] * b[k];
+        J->lam[p] = s;
+    }
+    return NULL;
+}
+
+void synth_lowrank_means(int64_t nnz, int32_t r, const double *wtT, const double *ftT, const int64_t *rows,
+                         const int64_t *cols, double *lam, int32_t nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    lam_job *jobs = (lam_job *)malloc(sizeof(lam_job) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].p0 = nnz * t / nthreads;
+        jobs[t].p1 = nnz * (t + 1) / nthreads;
+        jobs[t].r = r;
+        jobs[t].wtT = wtT;
+        jobs[t].ftT = ftT;
+        jobs[t].rows = rows;
+        jobs[t].cols = cols;
+        jobs[t].lam = lam;
+        pthread_create(&th[t], NULL, lam_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    free(jobs);
+}

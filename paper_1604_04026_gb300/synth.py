@@ -50,6 +50,8 @@ def _synth_lib():
         lib.synth_fetch.argtypes = [vp, vp, vp, vp]
         lib.synth_topics.restype = None
         lib.synth_topics.argtypes = [i64, i32, f64, u64, vp]
+        lib.synth_lowrank_means.restype = None
+        lib.synth_lowrank_means.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32]
         lib.synth_transpose.restype = None
         lib.synth_transpose.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp]
         _lib = lib
@@ -131,6 +133,35 @@ def poisson_lowrank(n: int, m: int, r: int, shape: float = 0.3, density: float =
     lam = wt.T @ ft
     v = np.where(mask, g.poisson(lam), 0).astype(np.float32)
     return from_dense(v)
+
+
+def poisson_lowrank_sparse(n: int, m: int, r: int, shape: float = 0.3, density: float = 0.01,
+                           seed: int = 0) -> CountMatrix:
+    """The law of poisson_lowrank (V_ij = M_ij * Poisson([Wt^T Ft]_ij),
+    Gamma(shape, 1) factors) drawn without the dense n x m matrix: per column
+    Binomial(n, density) rows drawn uniformly with replacement, duplicates
+    merged (so the mask is Bernoulli with a slightly lower rate at high
+    density), then the Poisson counts at those entries only (zeros dropped)."""
+    g = np.random.Generator(np.random.PCG64([seed, 0x5EED02]))
+    wt = g.gamma(shape, 1.0, size=(r, n))
+    ft = g.gamma(shape, 1.0, size=(r, m))
+    cnt = g.binomial(n, density, size=m)
+    cols = np.repeat(np.arange(m, dtype=np.int64), cnt)
+    key = np.sort(cols * n + g.integers(0, n, size=cols.size))
+    if key.size:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
+    cols, rows = key // n, key % n
+    lam = np.empty(cols.size)
+    wtT, ftT = np.ascontiguousarray(wt.T), np.ascontiguousarray(ft.T)
+    cols, rows = np.ascontiguousarray(cols), np.ascontiguousarray(rows)
+    _synth_lib().synth_lowrank_means(cols.size, r, _ptr(wtT), _ptr(ftT), _ptr(rows), _ptr(cols), _ptr(lam),
+                                     min(32, os.cpu_count() or 1))
+    v = g.poisson(lam).astype(np.float32)
+    keep = v > 0
+    cols, rows, v = cols[keep], rows[keep], v[keep]
+    colptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(cols, minlength=m), out=colptr[1:])
+    return from_csc(n, m, colptr, rows.astype(np.int32), v)
 
 
 def docs(n: int, m: int, K: int, zipf_s: float = 1.1, dir_a: float = 0.1,

@@ -27,6 +27,9 @@ from _util import (PROBE_FACTOR, RTOL, TIGHT, cfg_for, designed_matrix, fp32_sen
 
 pytestmark = pytest.mark.gpu
 
+# 1: dense tile kernels, 2: sparse-list kernels (0, the default, picks per half)
+LIST_MODES = [1, 2]
+
 BUCKET_LENGTHS = [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513,
                   1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 12000]
 
@@ -147,17 +150,20 @@ def _check_halves(V, W0, F0, Fg, Fo, Wg, Wo, F1, p, fraction=1.0, obj_rel=OBJ_RE
         assert (err <= obj_rel * scale + PROBE_FACTOR * d_dev).all(), (side, float((err / scale).max()))
 
 
-def test_halves_tight_every_bucket(designed):
-    """Unit lengths 0..12000 around every bucket edge (warp K=1..16, CTA, giant)."""
+@pytest.mark.parametrize("list_mode", LIST_MODES)
+def test_halves_tight_every_bucket(designed, list_mode):
+    """Unit lengths 0..12000 around every bucket edge (warp K=1..16, CTA,
+    clusters, giant; sparse-list warp, CTA and giant classes)."""
     V = designed
     r = 16
     W0, F0 = start(V, r, seed=2)
-    p = params(r, seed=5, **TIGHT)
+    p = params(r, seed=5, list_mode=list_mode, **TIGHT)
     _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
 
 
+@pytest.mark.parametrize("list_mode", LIST_MODES)
 @pytest.mark.parametrize("case", ["c1", "docs_r37", "reg"])
-def test_halves_tight(case, docs_small):
+def test_halves_tight(case, docs_small, list_mode):
     if case == "c1":
         V, r, extra = synth.poisson_lowrank(1000, 500, 10, seed=0), 10, {}
     elif case == "docs_r37":
@@ -165,7 +171,7 @@ def test_halves_tight(case, docs_small):
     else:
         V, r, extra = docs_small, 12, dict(alpha_W=0.5, beta_W=0.1, alpha_F=0.2, beta_F=0.3)
     W0, F0 = start(V, r, seed=7)
-    p = params(r, seed=11, **TIGHT, **extra)
+    p = params(r, seed=11, list_mode=list_mode, **TIGHT, **extra)
     _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
 
 
@@ -185,11 +191,12 @@ def test_r1_closed_form_on_gpu():
     m.close()
 
 
-def test_r256(docs_small):
+@pytest.mark.parametrize("list_mode", LIST_MODES)
+def test_r256(docs_small, list_mode):
     V = docs_small
     r = 256
     W0, F0 = start(V, r, seed=9)
-    p = params(r, seed=1, **TIGHT)
+    p = params(r, seed=1, list_mode=list_mode, **TIGHT)
     _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
 
 
@@ -211,14 +218,15 @@ def test_empty_units_go_to_zero():
 
 
 # ------------------------------------------------------------------ paper constants
+@pytest.mark.parametrize("list_mode", [0, 1, 2])
 @pytest.mark.parametrize("case", ["c1", "docs"])
-def test_kl_trajectory_20_sweeps(case, docs_small):
+def test_kl_trajectory_20_sweeps(case, docs_small, list_mode):
     if case == "c1":
         V, r = synth.poisson_lowrank(1000, 500, 10, seed=0), 10
     else:
         V, r = docs_small, 20
     W0, F0 = start(V, r, seed=0)
-    p = params(r, seed=0)
+    p = params(r, seed=0, list_mode=list_mode)
     m = model(V, W0, F0, p)
     traj, done = m.fit(20)
     assert done == 20
@@ -233,14 +241,15 @@ def test_kl_trajectory_20_sweeps(case, docs_small):
     m.close()
 
 
+@pytest.mark.parametrize("list_mode", LIST_MODES)
 @pytest.mark.parametrize("case", ["c1", "docs"])
-def test_halves_paper_constants(case, docs_small):
+def test_halves_paper_constants(case, docs_small, list_mode):
     """At eps_x = 0.1 a break or clamp decision can flip between FP32 and FP64
     for an entry sitting on its threshold: gate the fraction of entries and
     the per-unit objective."""
     V, r = (synth.poisson_lowrank(1000, 500, 10, seed=0), 10) if case == "c1" else (docs_small, 20)
     W0, F0 = start(V, r, seed=6)
-    p = params(r, seed=6)
+    p = params(r, seed=6, list_mode=list_mode)
     _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, fraction=0.995, obj_rel=1e-5)
 
 
@@ -308,12 +317,13 @@ def test_device_inputs_match_host(torch, docs_small):
     b.close()
 
 
-def test_runs_are_bitwise_reproducible(docs_small):
+@pytest.mark.parametrize("list_mode", [0, 1, 2])
+def test_runs_are_bitwise_reproducible(docs_small, list_mode):
     V, r = docs_small, 20
     W0, F0 = start(V, r, seed=2)
     out = []
     for _ in range(2):
-        m = model(V, W0, F0, params(r, seed=3))
+        m = model(V, W0, F0, params(r, seed=3, list_mode=list_mode))
         traj, _ = m.fit(3)
         out.append((traj, m.get_W(), m.get_F()))
         m.close()
@@ -346,7 +356,8 @@ def test_invalid_arguments(torch):
     m.close()
 
 
-def test_long_rows_every_cluster_size():
+@pytest.mark.parametrize("list_mode", LIST_MODES)
+def test_long_rows_every_cluster_size(list_mode):
     """Rows of 9k..99k nonzeros: CTA, cluster-of-2/4/8/16 and (beyond) giant
     kernels on the W half, against the oracle from an identical state."""
     rng = np.random.default_rng(4)
@@ -366,10 +377,11 @@ def test_long_rows_every_cluster_size():
     V = synth.from_csc(n, m, colptr, R.astype(np.int32), rng.integers(1, 6, size=R.size).astype(np.float32))
     r = 12
     W0, F0 = start(V, r, seed=3)
-    p = params(r, seed=8, **TIGHT)
+    p = params(r, seed=8, list_mode=list_mode, **TIGHT)
     m_ = model(V, W0, F0, p)
     kinds = {b["kernel"] for b in m_.plan() if b["side"] == 1}
     assert any(k.startswith("sweep_cluster") for k in kinds), kinds
+    assert "sparse_giant" in kinds and "sparse_cta512" in kinds, kinds
     m_.sweep_W(0)
     Wg = m_.get_W()
     m_.close()

@@ -51,14 +51,15 @@ def test_noalloc_matches_regular_twice():
     ldr = (r + 3) // 4 * 4
     W0 = synth.uniform_init(r, V.n, 3, 0)
     F0 = synth.uniform_init(r, V.m, 3, 1)
-    p = nk.default_params(r, seed=21)
+    p = nk.default_params(r, seed=21, list_mode=1)
 
     with nk.NMFKL(V.n, V.m, params=p) as model:
         model.set_data(V)
         model.init(W0, F0)
         model.sweep_F(4)
         F_ref = model.get_F()
-        assert {b["kernel"] for b in model.plan() if b["side"] == 0} == {"sweep_warp_k4"}
+        assert {b["kernel"] for b in model.plan() if b["side"] == 0 and b["kernel"].startswith("sweep_")} == \
+            {"sweep_warp_k4"}
 
     lib = _native.load()
     colptr = torch.from_numpy(V.colptr).cuda()
