@@ -986,7 +986,8 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 // Warp w of the group owns the chunks of 32 nonzeros c = w, w + NW, ...; its
 // lists hold only its own nonzeros, so warps never touch each other's state.
 // ---------------------------------------------------------------------------
-constexpr int kSparseE = 4;  // list entries per lane prefetched into registers
+constexpr int kSparseE = 4;   // list entries per lane prefetched into registers
+constexpr int kSparsePD = 3;  // coordinates whose lists are in flight
 
 struct SparseLayout {
     size_t words_off, cnt_off, red_off, xv_off, wq_off, tm_off, bytes;
@@ -1026,7 +1027,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 template <int NT>
 __host__ __device__ constexpr int sparse_min_blocks() {
-    return NT == 32 ? 3 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
+    return NT == 32 ? 2 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
 }
 template <int NT, bool kSmemState>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) sparse_kernel(HalfArgs a) {
@@ -1145,7 +1146,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
             const float4 *row = reinterpret_cast<const float4 *>(a.At + (int64_t)idx * ldr);
             float acc = 0.f;
             int terms = 0;
-            constexpr int kB = 4;
+            constexpr int kB = 8;
             for (int f0 = 0; f0 < nf4; f0 += kB) {
                 float4 buf[kB];
 #pragma unroll
@@ -1198,8 +1199,14 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
         group_sync();
 
         // ---- Algorithm 2 over this unit's coordinates, list entries only
-        int2 cur[E], nxt[E];
-        int ccur = 0, cnxt = 0;
+        // The lists of the next kSparsePD coordinates are in flight in
+        // registers: slot i of the pipeline holds position kk0 + i and is
+        // refilled with position kk0 + i + kSparsePD as soon as it is consumed
+        // (the loop over positions is unrolled by kSparsePD, so no register
+        // is copied while its load may still be outstanding).
+        constexpr int PD = kSparsePD;
+        int2 q[PD][E];
+        int qc[PD];
         auto fetch = [&](int pos, int2 (&dst)[E], int &cn) {
             cn = 0;
             if (pos < r) {
@@ -1213,57 +1220,63 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
                 }
             }
         };
-        fetch(0, cur, ccur);
-        for (int kk = 0; kk < r; ++kk) {
+#pragma unroll
+        for (int i = 0; i < PD; ++i) fetch(i, q[i], qc[i]);
+        // entries beyond the prefetched ones, four loads in flight per lane
+        auto for_rest = [&](const int2 *lk, int cn, auto &&body) {
+            for (int j0 = lane + 32 * E; j0 < cn; j0 += 128) {
+                int2 e[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) e[t] = j0 + 32 * t < cn ? __ldcg(lk + j0 + 32 * t) : make_int2(0, 0);
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (j0 + 32 * t < cn) body(e[t].x, __int_as_float(e[t].y));
+            }
+        };
+        auto coordinate = [&](int kk, int2 (&cur)[E], int cn) {
             const int k = perm[kk];
-            fetch(kk + 1, nxt, cnxt);
             const int2 *lk = mylists + (int64_t)k * LW;
-            const int cn = ccur;
             auto eval = [&]() -> float2 {
                 float sg = 0.f, sh = 0.f;
-#pragma unroll
-                for (int t = 0; t < E; ++t) {
-                    if (lane + 32 * t < cn) {
-                        const float av = __int_as_float(cur[t].y);
-                        const float2 s = wq[cur[t].x];
-                        sg = fmaf(s.x, av, sg);
-                        sh = fmaf(s.y * av, av, sh);
-                    }
-                }
-                for (int j = lane + 32 * E; j < cn; j += 32) {
-                    const int2 e = __ldcg(lk + j);
-                    const float av = __int_as_float(e.y);
-                    const float2 s = wq[e.x];
+                auto acc = [&](int p, float av) {
+                    const float2 s = wq[p];
                     sg = fmaf(s.x, av, sg);
                     sh = fmaf(s.y * av, av, sh);
-                }
-                return reduce(sg, sh);
-            };
-            auto update_one = [&](int p, float av, float d, int dc) {
-                const float2 s = xv[p];
-                int terms = dc != 0 ? (int)tm[p] : 0;
-                const float xn = step_x(s.x, av, d, dc, terms);
-                if (dc != 0) tm[p] = (uint16_t)terms;
-                const float ri = recip(xn + eps_div);
-                xv[p].x = xn;
-                wq[p] = make_float2(s.y * ri, s.y * ri * ri);
-            };
-            auto update = [&](float d, int dc) {
+                };
 #pragma unroll
                 for (int t = 0; t < E; ++t)
-                    if (lane + 32 * t < cn) update_one(cur[t].x, __int_as_float(cur[t].y), d, dc);
-                for (int j = lane + 32 * E; j < cn; j += 32) {
-                    const int2 e = __ldcg(lk + j);
-                    update_one(e.x, __int_as_float(e.y), d, dc);
-                }
+                    if (lane + 32 * t < cn) acc(cur[t].x, __int_as_float(cur[t].y));
+                for_rest(lk, cn, acc);
+                return reduce(sg, sh);
+            };
+            auto update = [&](float d, int dc) {
+                auto upd = [&](int p, float av) {
+                    const float2 s = xv[p];
+                    int terms = dc != 0 ? (int)tm[p] : 0;
+                    const float xn = step_x(s.x, av, d, dc, terms);
+                    if (dc != 0) tm[p] = (uint16_t)terms;
+                    const float ri = recip(xn + eps_div);
+                    xv[p].x = xn;
+                    wq[p] = make_float2(s.y * ri, s.y * ri * ri);
+                };
+#pragma unroll
+                for (int t = 0; t < E; ++t)
+                    if (lane + 32 * t < cn) upd(cur[t].x, __int_as_float(cur[t].y));
+                for_rest(lk, cn, upd);
                 // the next evaluation may read these entries from other lanes
                 __syncwarp();
             };
             const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
             if (tid_g == 0) x_out[k] = xk;
+        };
+        for (int kk0 = 0; kk0 < r; kk0 += PD) {
 #pragma unroll
-            for (int t = 0; t < E; ++t) cur[t] = nxt[t];
-            ccur = cnxt;
+            for (int i = 0; i < PD; ++i) {
+                if (kk0 + i < r) {
+                    coordinate(kk0 + i, q[i], qc[i]);
+                    fetch(kk0 + i + PD, q[i], qc[i]);
+                }
+            }
         }
         if (a.unit_obj) {
             float t = 0.f;
@@ -1378,7 +1391,7 @@ const SparseKind kSparseKinds[] = {
     {(const void *)sparse_kernel<128, true>, 128, 1024, "sparse_cta128"},
     {(const void *)sparse_kernel<256, true>, 256, 2048, "sparse_cta256"},
     {(const void *)sparse_kernel<512, true>, 512, 8192, "sparse_cta512"},
-    {(const void *)sparse_kernel<1024, false>, 1024, 0, "sparse_giant"},
+    {(const void *)sparse_kernel<512, false>, 512, 0, "sparse_giant"},
 };
 constexpr int kNumSparseKinds = sizeof(kSparseKinds) / sizeof(kSparseKinds[0]);
 
