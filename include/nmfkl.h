@@ -254,7 +254,8 @@ nmfkl_status nmfkl_debug_perm(nmfkl_ctx *ctx, int64_t sweep, int32_t side, int64
  *   Wt float[n * ldr]: W unit-major (row i holds W[0..r-1, i]), ldr =
  *     4 * ceil(r / 4), padding entries 0;
  *   Ft float[m * ldr]: F unit-major, read as the start and overwritten.
- * Parameters as in nmfkl_params (side F: alpha_F, beta_F). max_len bounds
+ * Parameters as in nmfkl_params (side F: alpha_F, beta_F; list_mode is
+ * ignored: this path always runs the dense-tile warp kernels). max_len bounds
  * the nonzeros of every column; limits: r <= 256 and max_len <= 256 (EINVAL
  * beyond them; a column longer than max_len is reported as EINVAL after the
  * launch and left unchanged). Synchronizes `stream` (a cudaStream_t or NULL)

@@ -58,7 +58,7 @@ __host__ __device__ inline RingLayout ring_layout(int r, int ldr, int nt, int k,
     g.ring_off = off;
     off = align16(off + (size_t)d * nt * k * 4);
     g.red_off = off;
-    if (cta) off = align16(off + 2 * ((size_t)nt / 32) * sizeof(float2));
+    if (cta) off = align16(off + 2 * ((size_t)nt / 32) * sizeof(float4));
     g.bytes = off;
     return g;
 }
@@ -67,6 +67,11 @@ __host__ __device__ inline RingLayout ring_layout(int r, int ldr, int nt, int k,
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+// 16-byte global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -179,15 +184,17 @@ __device__ __forceinline__ Staged stage_lane(const HalfArgs &a, float *tile, con
     return Staged{acc, cnt};
 }
 
+// Work counters of one thread (flushed once per kernel; a group processes far
+// fewer than 2^32 coordinates).
 struct Tally {
-    unsigned long long coords = 0, evals = 0, steps = 0, caps = 0;
+    unsigned coords = 0, evals = 0, steps = 0, caps = 0;
 };
 
 __device__ __forceinline__ void flush_tally(const HalfArgs &a, const Tally &t) {
-    if (t.coords) atomicAdd(&a.counters[0], t.coords);
-    if (t.evals) atomicAdd(&a.counters[1], t.evals);
-    if (t.steps) atomicAdd(&a.counters[2], t.steps);
-    if (t.caps) atomicAdd(&a.counters[3], t.caps);
+    if (t.coords) atomicAdd(&a.counters[0], (unsigned long long)t.coords);
+    if (t.evals) atomicAdd(&a.counters[1], (unsigned long long)t.evals);
+    if (t.steps) atomicAdd(&a.counters[2], (unsigned long long)t.steps);
+    if (t.caps) atomicAdd(&a.counters[3], (unsigned long long)t.caps);
 }
 
 // Drops the L2 lines of a finished tile (r rows of `len` floats, row stride
@@ -219,24 +226,27 @@ __device__ __forceinline__ double warp_sum_d(double t) {
 // (sum_p w_p A_pk, sum_p q_p A_pk^2) over the subproblem; update(d, dc)
 // applies x_p += d A_pk (dc: x_k became positive (+1) or zero (-1)). Every
 // thread of the group runs it with identical values.
+// `first`, when has_first is set, is the coordinate's first evaluation,
+// already computed (in a batch with the next coordinate; see run_coordinates).
 template <class Eval, class Update>
 __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, float sAk, Eval &&eval,
-                                                   Update &&update, Tally &t) {
+                                                   Update &&update, Tally &t, bool has_first = false,
+                                                   float2 first = float2{0.f, 0.f}) {
     const float alpha = a.alpha, beta = a.beta;
-    float2 s = eval();
-    ++t.evals;
-    ++t.coords;
-    float g = -s.x + sAk + alpha * xk + beta;
-    float h = s.y + alpha;
     const float tol = a.grad_mode == 0 ? a.eps_grad * (sAk + beta) : a.eps_grad;
     const float xfloor = a.grad_mode == 0 ? 0.f : a.eps_grad;
-    int it = 0;
-    while (g < -tol || (fabsf(g) > tol && xk > xfloor)) {
+    ++t.coords;
+    // one evaluation site: every pass evaluates, tests, and steps
+    for (int it = 0;; ++it) {
+        const float2 s = (it == 0 && has_first) ? first : eval();
+        ++t.evals;
+        const float g = -s.x + sAk + alpha * xk + beta;
+        const float h = s.y + alpha;
+        if (!(g < -tol || (fabsf(g) > tol && xk > xfloor))) break;
         if (it == a.max_inner) {
             ++t.caps;
             break;
         }
-        ++it;
         float xn;
         if (h > 0.f) {
             xn = xk - __fdiv_rn(g, h);
@@ -253,10 +263,6 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
         ++t.steps;
         const bool brk = a.break_mode == 0 ? (fabsf(d) < a.eps_x * xs) : (d < a.eps_x * xs);
         if (brk) break;
-        s = eval();
-        ++t.evals;
-        g = -s.x + sAk + alpha * xk + beta;
-        h = s.y + alpha;
     }
     return xk;
 }
@@ -270,7 +276,7 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
 // SM) except the widest warp kernel.
 template <int NT, int K>
 __host__ __device__ constexpr int min_blocks() {
-    return NT == 32 ? (K <= 4 ? 3 : (K <= 8 ? 2 : 1)) : (512 / NT > 1 ? 512 / NT : 1);
+    return NT == 32 ? (K <= 4 ? 3 : 2) : (512 / NT > 1 ? 512 / NT : 1);
 }
 // Kernel modes: one half sweep, the allocation-free F half (units are the
 // column indices themselves), and fold-in (each column runs its own sweeps of
@@ -312,16 +318,20 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
     auto group_sync = [&]() {
         if constexpr (kCta) __syncthreads(); else __syncwarp();
     };
+    // Every CTA reduction (reduce, reduce2, group_sum_d) uses 16-byte slots,
+    // one per warp, in two halves used alternately (parity), so that a warp
+    // that runs ahead never overwrites partials another warp still reads.
+    float4 *red4 = reinterpret_cast<float4 *>(red);
     // Sum of one double per thread over the group, identical in every thread.
     auto group_sum_d = [&](double t) -> double {
         t = warp_sum_d(t);
         if constexpr (kCta) {
-            double *rd = reinterpret_cast<double *>(red + parity * kNW);
-            if (lane == 0) rd[warp_in_block] = t;
+            float4 *rb = red4 + parity * kNW;
+            if (lane == 0) *reinterpret_cast<double *>(&rb[warp_in_block]) = t;
             __syncthreads();
             double tot = 0.0;
 #pragma unroll
-            for (int w = 0; w < kNW; ++w) tot += rd[w];
+            for (int w = 0; w < kNW; ++w) tot += *reinterpret_cast<const double *>(&rb[w]);
             parity ^= 1;
             return tot;
         } else {
@@ -422,13 +432,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                     sh += __shfl_xor_sync(kFull, sh, o);
                 }
                 if constexpr (kCta) {
-                    float2 *rb = red + parity * kNW;
-                    if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
+                    float4 *rb = red4 + parity * kNW;
+                    if (lane == 0) rb[warp_in_block] = make_float4(sg, sh, 0.f, 0.f);
                     __syncthreads();
                     float tg = 0.f, th = 0.f;
 #pragma unroll
                     for (int w = 0; w < kNW; ++w) {
-                        const float2 v = rb[w];
+                        const float4 v = rb[w];
                         tg += v.x;
                         th += v.y;
                     }
@@ -438,13 +448,74 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                     return make_float2(sg, sh);
                 }
             };
+            // Both sums of two coordinates at once (identical, bit for bit, to
+            // two reduce() calls).
+            auto reduce2 = [&](float4 v) -> float4 {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v.x += __shfl_xor_sync(kFull, v.x, o);
+                    v.y += __shfl_xor_sync(kFull, v.y, o);
+                    v.z += __shfl_xor_sync(kFull, v.z, o);
+                    v.w += __shfl_xor_sync(kFull, v.w, o);
+                }
+                if constexpr (kCta) {
+                    float4 *rb = red4 + parity * kNW;
+                    if (lane == 0) rb[warp_in_block] = v;
+                    __syncthreads();
+                    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int w = 0; w < kNW; ++w) {
+                        const float4 u = rb[w];
+                        t.x += u.x;
+                        t.y += u.y;
+                        t.z += u.z;
+                        t.w += u.w;
+                    }
+                    parity ^= 1;
+                    return t;
+                } else {
+                    return v;
+                }
+            };
+            // Coordinates at zero whose derivative points outward stay at zero
+            // and change nothing; two such consecutive coordinates are
+            // evaluated together, and the second evaluation is used only if
+            // the first coordinate did not move (then it is exactly what a
+            // sequential evaluation would give).
 #pragma unroll
             for (int i = 0; i < D - 1; ++i) issue(i);
-            for (int kk = 0; kk < r; ++kk) {
-                issue(kk + D - 1);
-                cp_async_wait<D - 1>();
-                const float *ac = myring + (kk % D) * K * NT;
+            int issued = D - 1;
+            for (int kk = 0; kk < r;) {
+                while (issued < kk + D) issue(issued++);
                 const int k = perm[kk];
+                const bool pair = kk + 1 < r && x_init[k] == 0.f && x_init[perm[kk + 1]] == 0.f;
+                float2 first1 = make_float2(0.f, 0.f);
+                bool has0 = false;
+                float2 first0 = make_float2(0.f, 0.f);
+                if (pair) {
+                    cp_async_wait<D - 2>();
+                    const float *a0 = myring + (kk % D) * K * NT;
+                    const float *a1 = myring + ((kk + 1) % D) * K * NT;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int s = 0; s < K; ++s) {
+                        if (s < ks) {
+                            const float av0 = a0[s * NT], av1 = a1[s * NT];
+                            v.x = fmaf(wr[s], av0, v.x);
+                            v.y = fmaf(qr[s] * av0, av0, v.y);
+                            v.z = fmaf(wr[s], av1, v.z);
+                            v.w = fmaf(qr[s] * av1, av1, v.w);
+                        }
+                    }
+                    v = reduce2(v);
+                    has0 = true;
+                    first0 = make_float2(v.x, v.y);
+                    first1 = make_float2(v.z, v.w);
+                } else {
+                    cp_async_wait<D - 1>();
+                }
+                const float *ac = myring + (kk % D) * K * NT;
+                bool moved = false;
                 auto eval = [&]() -> float2 {
                     float sg = 0.f, sh = 0.f;
 #pragma unroll
@@ -458,6 +529,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                     return reduce(sg, sh);
                 };
                 auto update = [&](float d, int dc) {
+                    moved = true;
 #pragma unroll
                     for (int s = 0; s < K; ++s) {
                         if (s < ks) {
@@ -468,8 +540,40 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                         }
                     }
                 };
-                const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+                const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally, has0, first0);
                 if (tid_g == 0) x_out[k] = xk;
+                ++kk;
+                if (pair && !moved) {
+                    // the second coordinate of the pair, from its batched evaluation
+                    const float *ac1 = myring + (kk % D) * K * NT;
+                    const int k1 = perm[kk];
+                    auto eval1 = [&]() -> float2 {
+                        float sg = 0.f, sh = 0.f;
+#pragma unroll
+                        for (int s = 0; s < K; ++s) {
+                            if (s < ks) {
+                                const float av = ac1[s * NT];
+                                sg = fmaf(wr[s], av, sg);
+                                sh = fmaf(qr[s] * av, av, sh);
+                            }
+                        }
+                        return reduce(sg, sh);
+                    };
+                    auto update1 = [&](float d, int dc) {
+#pragma unroll
+                        for (int s = 0; s < K; ++s) {
+                            if (s < ks) {
+                                xr[s] = step_x(xr[s], ac1[s * NT], d, dc, cr[s]);
+                                const float ri = recip(xr[s] + eps_div);
+                                wr[s] = vr[s] * ri;
+                                qr[s] = wr[s] * ri;
+                            }
+                        }
+                    };
+                    const float xk1 = newton_coordinate(a, x_init[k1], a.sumA[k1], eval1, update1, tally, true, first1);
+                    if (tid_g == 0) x_out[k1] = xk1;
+                    ++kk;
+                }
             }
             cp_async_wait<0>();
         };
@@ -986,13 +1090,15 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 // Warp w of the group owns the chunks of 32 nonzeros c = w, w + NW, ...; its
 // lists hold only its own nonzeros, so warps never touch each other's state.
 // ---------------------------------------------------------------------------
-constexpr int kSparseE = 4;   // list entries per lane prefetched into registers
-constexpr int kSparsePD = 3;  // coordinates whose lists are in flight
+constexpr int kSparseE = 4;  // list entries per lane prefetched into registers
+
+constexpr int kSparseCapW = 256;  // list entries per warp staged in shared memory per coordinate
 
 struct SparseLayout {
-    size_t words_off, cnt_off, red_off, xv_off, wq_off, tm_off, bytes;
+    size_t words_off, cnt_off, red_off, xv_off, wq_off, tm_off, lbuf_off, bytes;
 };
-// scap: nonzeros whose state is in shared memory (0: state in the slot)
+// scap: nonzeros whose state is in shared memory (0: state in the slot, and a
+// double-buffered shared copy of each warp's list for the current coordinate)
 __host__ __device__ inline SparseLayout sparse_layout(int r, int ldr, int nt, int scap) {
     SparseLayout g{};
     size_t off = align16(256 + 2 * (size_t)ldr * 4);  // perm | x_init | x_out
@@ -1002,20 +1108,25 @@ __host__ __device__ inline SparseLayout sparse_layout(int r, int ldr, int nt, in
     off = align16(off + 4 * (size_t)(nt / 32) * ldr);
     g.red_off = off;
     off = align16(off + 2 * (size_t)(nt / 32) * sizeof(float2));
+    // state slots: the scap nonzeros and one dummy (index scap)
+    const size_t ns = scap > 0 ? (size_t)scap + 1 : 0;
     g.xv_off = off;
-    off = align16(off + 8 * (size_t)scap);
+    off = align16(off + 8 * ns);
     g.wq_off = off;
-    off = align16(off + 8 * (size_t)scap);
+    off = align16(off + 8 * ns);
     g.tm_off = off;
-    off = align16(off + 2 * (size_t)scap);
+    off = align16(off + 2 * ns);
+    g.lbuf_off = off;
+    if (scap == 0) off = align16(off + 2 * (size_t)(nt / 32) * kSparseCapW * sizeof(int2));
     g.bytes = off;
     return g;
 }
 // Scratch slot of a sparse group (floats): lists [NW][r][lcap/NW] of int2,
-// then, for giant units, the state xv[lcap], wq[lcap] (float2) and tm[lcap].
+// then, when the state is not in shared memory, xv[lcap+1], wq[lcap+1]
+// (float2) and tm[lcap+1] (the last of each is the dummy).
 __host__ __device__ inline int64_t sparse_slot_floats(int r, int lcap, bool smem_state) {
     int64_t f = 2 * (int64_t)r * lcap;
-    if (!smem_state) f += 4 * (int64_t)lcap + (lcap + 1) / 2;
+    if (!smem_state) f += 4 * ((int64_t)lcap + 1) + (lcap + 2) / 2;
     return (f + 63) / 64 * 64;
 }
 
@@ -1063,14 +1174,19 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
         tm = reinterpret_cast<uint16_t *>(gs + lay.tm_off);
     } else {
         xv = reinterpret_cast<float2 *>(slot + 2 * (int64_t)r * lcap);
-        wq = xv + lcap;
-        tm = reinterpret_cast<uint16_t *>(wq + lcap);
+        wq = xv + lcap + 1;
+        tm = reinterpret_cast<uint16_t *>(wq + lcap + 1);
     }
     __shared__ int s_q;
     const float eps_div = a.eps_div;
     const int count = a.count_dev ? *a.count_dev : a.count;
     Tally tally;
     int parity = 0;
+    if (tid_g == 0) {  // the dummy entry's state: zero, and it stays zero
+        xv[lcap] = make_float2(0.f, 0.f);
+        wq[lcap] = make_float2(0.f, 0.f);
+        tm[lcap] = 0;
+    }
 
     auto group_sync = [&]() {
         if constexpr (kCta) __syncthreads(); else __syncwarp();
@@ -1199,84 +1315,156 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
         group_sync();
 
         // ---- Algorithm 2 over this unit's coordinates, list entries only
-        // The lists of the next kSparsePD coordinates are in flight in
-        // registers: slot i of the pipeline holds position kk0 + i and is
-        // refilled with position kk0 + i + kSparsePD as soon as it is consumed
-        // (the loop over positions is unrolled by kSparsePD, so no register
-        // is copied while its load may still be outstanding).
-        constexpr int PD = kSparsePD;
-        int2 q[PD][E];
-        int qc[PD];
-        auto fetch = [&](int pos, int2 (&dst)[E], int &cn) {
-            cn = 0;
-            if (pos < r) {
-                const int k = perm[pos];
-                cn = mycnt[k];
+        // ---- Algorithm 2 over this unit's coordinates, list entries only
+        if constexpr (kSmemState) {
+            // The list of the next coordinate is in flight in registers while
+            // the current one is processed (two register sets used in turn, so
+            // no register is copied while its load may be outstanding).
+            int2 qa[E], qb[E];
+            int ca = 0, cb = 0;
+            auto fetch = [&](int pos, int2 (&dst)[E], int &cn) {
+                cn = 0;
+                if (pos < r) {
+                    const int k = perm[pos];
+                    cn = mycnt[k];
+                    const int2 *lk = mylists + (int64_t)k * LW;
+#pragma unroll
+                    for (int t = 0; t < E; ++t) {
+                        const int j = lane + 32 * t;
+                        dst[t] = j < cn ? __ldcg(lk + j) : make_int2(0, 0);
+                    }
+                }
+            };
+            // entries beyond the prefetched ones, four loads in flight per lane
+            auto for_rest = [&](const int2 *lk, int cn, auto &&body) {
+                for (int j0 = lane + 32 * E; j0 < cn; j0 += 128) {
+                    int2 e[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) e[t] = j0 + 32 * t < cn ? __ldcg(lk + j0 + 32 * t) : make_int2(0, 0);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (j0 + 32 * t < cn) body(e[t].x, __int_as_float(e[t].y));
+                }
+            };
+            auto coordinate = [&](int kk, int2 (&cur)[E], int cn) {
+                const int k = perm[kk];
                 const int2 *lk = mylists + (int64_t)k * LW;
+                auto eval = [&]() -> float2 {
+                    float sg = 0.f, sh = 0.f;
+                    auto acc = [&](int p, float av) {
+                        const float2 st = wq[p];
+                        sg = fmaf(st.x, av, sg);
+                        sh = fmaf(st.y * av, av, sh);
+                    };
 #pragma unroll
-                for (int t = 0; t < E; ++t) {
-                    const int j = lane + 32 * t;
-                    dst[t] = j < cn ? __ldcg(lk + j) : make_int2(0, 0);
+                    for (int t = 0; t < E; ++t)
+                        if (lane + 32 * t < cn) acc(cur[t].x, __int_as_float(cur[t].y));
+                    for_rest(lk, cn, acc);
+                    return reduce(sg, sh);
+                };
+                auto update = [&](float d, int dc) {
+                    auto upd = [&](int p, float av) {
+                        const float2 st = xv[p];
+                        int terms = dc != 0 ? (int)tm[p] : 0;
+                        const float xn = step_x(st.x, av, d, dc, terms);
+                        if (dc != 0) tm[p] = (uint16_t)terms;
+                        const float ri = recip(xn + eps_div);
+                        xv[p].x = xn;
+                        wq[p] = make_float2(st.y * ri, st.y * ri * ri);
+                    };
+#pragma unroll
+                    for (int t = 0; t < E; ++t)
+                        if (lane + 32 * t < cn) upd(cur[t].x, __int_as_float(cur[t].y));
+                    for_rest(lk, cn, upd);
+                    // the next evaluation may read these entries from other lanes
+                    __syncwarp();
+                };
+                const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+                if (tid_g == 0) x_out[k] = xk;
+            };
+            fetch(0, qa, ca);
+            for (int kk = 0; kk < r; kk += 2) {
+                fetch(kk + 1, qb, cb);
+                coordinate(kk, qa, ca);
+                if (kk + 1 < r) {
+                    fetch(kk + 2, qa, ca);
+                    coordinate(kk + 1, qb, cb);
                 }
             }
-        };
-#pragma unroll
-        for (int i = 0; i < PD; ++i) fetch(i, q[i], qc[i]);
-        // entries beyond the prefetched ones, four loads in flight per lane
-        auto for_rest = [&](const int2 *lk, int cn, auto &&body) {
-            for (int j0 = lane + 32 * E; j0 < cn; j0 += 128) {
-                int2 e[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) e[t] = j0 + 32 * t < cn ? __ldcg(lk + j0 + 32 * t) : make_int2(0, 0);
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (j0 + 32 * t < cn) body(e[t].x, __int_as_float(e[t].y));
-            }
-        };
-        auto coordinate = [&](int kk, int2 (&cur)[E], int cn) {
-            const int k = perm[kk];
-            const int2 *lk = mylists + (int64_t)k * LW;
-            auto eval = [&]() -> float2 {
-                float sg = 0.f, sh = 0.f;
-                auto acc = [&](int p, float av) {
-                    const float2 s = wq[p];
-                    sg = fmaf(s.x, av, sg);
-                    sh = fmaf(s.y * av, av, sh);
-                };
-#pragma unroll
-                for (int t = 0; t < E; ++t)
-                    if (lane + 32 * t < cn) acc(cur[t].x, __int_as_float(cur[t].y));
-                for_rest(lk, cn, acc);
-                return reduce(sg, sh);
+        } else {
+            // State in the slot: each warp copies the list of the next
+            // coordinate into shared memory (cp.async, up to kSparseCapW
+            // entries) while it works on the current one, and issues the state
+            // loads eight at a time.
+            int2 *lbuf = reinterpret_cast<int2 *>(gs + lay.lbuf_off) + (size_t)w * 2 * kSparseCapW;
+            auto stage_list = [&](int pos) {
+                if (pos < r) {
+                    const int k = perm[pos];
+                    const int cn = min(mycnt[k], kSparseCapW);
+                    const int2 *src = mylists + (int64_t)k * LW;
+                    int2 *dst = lbuf + (pos & 1) * kSparseCapW;
+                    for (int c = lane; 2 * c < cn; c += 32) cp_async16(dst + 2 * c, src + 2 * c);
+                }
+                cp_async_commit();
             };
-            auto update = [&](float d, int dc) {
-                auto upd = [&](int p, float av) {
-                    const float2 s = xv[p];
-                    int terms = dc != 0 ? (int)tm[p] : 0;
-                    const float xn = step_x(s.x, av, d, dc, terms);
-                    if (dc != 0) tm[p] = (uint16_t)terms;
-                    const float ri = recip(xn + eps_div);
-                    xv[p].x = xn;
-                    wq[p] = make_float2(s.y * ri, s.y * ri * ri);
-                };
-#pragma unroll
-                for (int t = 0; t < E; ++t)
-                    if (lane + 32 * t < cn) upd(cur[t].x, __int_as_float(cur[t].y));
-                for_rest(lk, cn, upd);
-                // the next evaluation may read these entries from other lanes
+            constexpr int kU = 8;
+            stage_list(0);
+            for (int kk = 0; kk < r; ++kk) {
+                stage_list(kk + 1);
+                cp_async_wait<1>();
                 __syncwarp();
-            };
-            const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
-            if (tid_g == 0) x_out[k] = xk;
-        };
-        for (int kk0 = 0; kk0 < r; kk0 += PD) {
+                const int k = perm[kk];
+                const int cn = mycnt[k];
+                const int2 *lk = mylists + (int64_t)k * LW;
+                const int2 *lb = lbuf + (kk & 1) * kSparseCapW;
+                auto entry = [&](int j) -> int2 { return j < kSparseCapW ? lb[j] : __ldcg(lk + j); };
+                auto eval = [&]() -> float2 {
+                    float sg = 0.f, sh = 0.f;
+                    for (int j0 = lane; j0 < cn; j0 += 32 * kU) {
+                        int2 e[kU];
+                        float2 st[kU];
 #pragma unroll
-            for (int i = 0; i < PD; ++i) {
-                if (kk0 + i < r) {
-                    coordinate(kk0 + i, q[i], qc[i]);
-                    fetch(kk0 + i + PD, q[i], qc[i]);
-                }
+                        for (int t = 0; t < kU; ++t) e[t] = j0 + 32 * t < cn ? entry(j0 + 32 * t) : make_int2(0, 0);
+#pragma unroll
+                        for (int t = 0; t < kU; ++t) st[t] = j0 + 32 * t < cn ? wq[e[t].x] : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int t = 0; t < kU; ++t) {
+                            const float av = __int_as_float(e[t].y);
+                            sg = fmaf(st[t].x, av, sg);
+                            sh = fmaf(st[t].y * av, av, sh);
+                        }
+                    }
+                    return reduce(sg, sh);
+                };
+                auto update = [&](float d, int dc) {
+                    for (int j0 = lane; j0 < cn; j0 += 32 * kU) {
+                        int2 e[kU];
+                        float2 st[kU];
+#pragma unroll
+                        for (int t = 0; t < kU; ++t) e[t] = j0 + 32 * t < cn ? entry(j0 + 32 * t) : make_int2(0, 0);
+#pragma unroll
+                        for (int t = 0; t < kU; ++t) st[t] = j0 + 32 * t < cn ? xv[e[t].x] : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int t = 0; t < kU; ++t) {
+                            if (j0 + 32 * t < cn) {
+                                const int p = e[t].x;
+                                int terms = dc != 0 ? (int)tm[p] : 0;
+                                const float xn = step_x(st[t].x, __int_as_float(e[t].y), d, dc, terms);
+                                if (dc != 0) tm[p] = (uint16_t)terms;
+                                const float ri = recip(xn + eps_div);
+                                xv[p].x = xn;
+                                wq[p] = make_float2(st[t].y * ri, st[t].y * ri * ri);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                };
+                const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+                if (tid_g == 0) x_out[k] = xk;
+                // the buffer just read is refilled two coordinates on
+                __syncwarp();
             }
+            cp_async_wait<0>();
         }
         if (a.unit_obj) {
             float t = 0.f;
@@ -1382,16 +1570,19 @@ int active_clusters(int cl, size_t smem) {
 
 struct SparseKind {
     const void *fn;
-    int nt;      // threads per group (32: warp groups, several per block)
-    int cap;     // longest unit (nonzeros) of the class; 0: no limit (state in the slot)
+    int nt;          // threads per group (32: warp groups, several per block)
+    int cap;         // longest unit (nonzeros) of the class; 0: no limit
+    bool smem;       // per-nonzero state in shared memory (else in the slot)
+    int max_groups;  // resident groups per SM at most (0: as many as fit)
     const char *name;
 };
+// One warp per unit up to 8,192 nonzeros (state in shared memory up to 512,
+// in the slot beyond), one 512-thread CTA per unit past that.
 const SparseKind kSparseKinds[] = {
-    {(const void *)sparse_kernel<32, true>, 32, 512, "sparse_warp"},
-    {(const void *)sparse_kernel<128, true>, 128, 1024, "sparse_cta128"},
-    {(const void *)sparse_kernel<256, true>, 256, 2048, "sparse_cta256"},
-    {(const void *)sparse_kernel<512, true>, 512, 8192, "sparse_cta512"},
-    {(const void *)sparse_kernel<512, false>, 512, 0, "sparse_giant"},
+    {(const void *)sparse_kernel<32, true>, 32, 512, true, 0, "sparse_warp"},
+    {(const void *)sparse_kernel<32, false>, 32, 2048, false, 0, "sparse_warp_g2k"},
+    {(const void *)sparse_kernel<32, false>, 32, 8192, false, 8, "sparse_warp_g8k"},
+    {(const void *)sparse_kernel<512, false>, 512, 0, false, 0, "sparse_giant"},
 };
 constexpr int kNumSparseKinds = sizeof(kSparseKinds) / sizeof(kSparseKinds[0]);
 
@@ -1441,7 +1632,7 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
             return (ptr[x + 1] - ptr[x]) > (ptr[y + 1] - ptr[y]);
         });
         const SparseKind &sk = kSparseKinds[kind];
-        const bool smem_state = sk.cap > 0;
+        const bool smem_state = sk.smem;
         const bool cta = sk.nt > 32;
         Bucket b{};
         b.sparse = true;
@@ -1473,6 +1664,7 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
             c->err = std::string("kernel ") + sk.name + " cannot be resident";
             return NMFKL_EINVAL;
         }
+        if (sk.max_groups > 0) per_sm = std::max(1, std::min(per_sm, sk.max_groups / gpb));
         const int64_t need_blocks = (b.count + gpb - 1) / gpb;
         b.grid = (int)std::min<int64_t>(need_blocks, (int64_t)per_sm * c->num_sms);
         b.groups = b.grid * gpb;

@@ -381,7 +381,7 @@ def test_long_rows_every_cluster_size(list_mode):
     m_ = model(V, W0, F0, p)
     kinds = {b["kernel"] for b in m_.plan() if b["side"] == 1}
     assert any(k.startswith("sweep_cluster") for k in kinds), kinds
-    assert "sparse_giant" in kinds and "sparse_cta512" in kinds, kinds
+    assert "sparse_giant" in kinds and "sparse_warp_g8k" in kinds, kinds
     m_.sweep_W(0)
     Wg = m_.get_W()
     m_.close()
