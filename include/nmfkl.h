@@ -214,7 +214,8 @@ nmfkl_status nmfkl_set_timing(nmfkl_ctx *ctx, int32_t enable);
 int32_t nmfkl_kernel_times(nmfkl_ctx *ctx, const char **names, int64_t *launches, double *ms,
                            int32_t cap, int32_t reset);
 
-/* Launch plan of the sweep kernels: one entry per length bucket and half. */
+/* Launch plans of the sweep kernels: one entry per length bucket, half and
+ * path (each half has a dense-tile plan and a sparse-list plan). */
 typedef struct {
     const char *kernel;  /* kernel family name (static storage) */
     int32_t side;        /* 0 = F half (columns), 1 = W half (rows) */
@@ -223,6 +224,8 @@ typedef struct {
     int64_t max_len;     /* longest unit */
     int32_t grid, block; /* persistent launch shape */
     int64_t smem;        /* dynamic shared memory per block, bytes */
+    int32_t ran_last;    /* 1 if the last half of this side ran this bucket's plan
+                            (dense tile or sparse lists, see list_mode) */
 } nmfkl_bucket_info;
 
 /* Fills up to `cap` entries; returns the number of buckets (-1 on a NULL ctx). */

@@ -207,7 +207,8 @@ class NMFKL:
         nb = self._lib.nmfkl_plan_info(self._h, arr, cap)
         return [{"kernel": arr[i].kernel.decode(), "side": arr[i].side, "count": arr[i].count,
                  "nnz": arr[i].nnz, "max_len": arr[i].max_len, "grid": arr[i].grid,
-                 "block": arr[i].block, "smem": arr[i].smem} for i in range(min(nb, cap))]
+                 "block": arr[i].block, "smem": arr[i].smem, "ran_last": bool(arr[i].ran_last)}
+                for i in range(min(nb, cap))]
 
     def _get(self, fn, rows, cols, out):
         if out is None:

@@ -620,6 +620,7 @@ int32_t nmfkl_plan_info(const nmfkl_ctx *c, nmfkl_bucket_info *out, int32_t cap)
                 out[i].grid = b.grid;
                 out[i].block = b.block;
                 out[i].smem = (int64_t)b.smem;
+                out[i].ran_last = c->used_sparse[side] == (b.sparse ? 1 : 0) ? 1 : 0;
             }
             ++i;
         }

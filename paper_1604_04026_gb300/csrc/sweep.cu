@@ -226,19 +226,16 @@ __device__ __forceinline__ double warp_sum_d(double t) {
 // (sum_p w_p A_pk, sum_p q_p A_pk^2) over the subproblem; update(d, dc)
 // applies x_p += d A_pk (dc: x_k became positive (+1) or zero (-1)). Every
 // thread of the group runs it with identical values.
-// `first`, when has_first is set, is the coordinate's first evaluation,
-// already computed (in a batch with the next coordinate; see run_coordinates).
 template <class Eval, class Update>
 __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, float sAk, Eval &&eval,
-                                                   Update &&update, Tally &t, bool has_first = false,
-                                                   float2 first = float2{0.f, 0.f}) {
+                                                   Update &&update, Tally &t) {
     const float alpha = a.alpha, beta = a.beta;
     const float tol = a.grad_mode == 0 ? a.eps_grad * (sAk + beta) : a.eps_grad;
     const float xfloor = a.grad_mode == 0 ? 0.f : a.eps_grad;
     ++t.coords;
     // one evaluation site: every pass evaluates, tests, and steps
     for (int it = 0;; ++it) {
-        const float2 s = (it == 0 && has_first) ? first : eval();
+        const float2 s = eval();
         ++t.evals;
         const float g = -s.x + sAk + alpha * xk + beta;
         const float h = s.y + alpha;
@@ -318,7 +315,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
     auto group_sync = [&]() {
         if constexpr (kCta) __syncthreads(); else __syncwarp();
     };
-    // Every CTA reduction (reduce, reduce2, group_sum_d) uses 16-byte slots,
+    // Every CTA reduction (reduce, group_sum_d) uses 16-byte slots,
     // one per warp, in two halves used alternately (parity), so that a warp
     // that runs ahead never overwrites partials another warp still reads.
     float4 *red4 = reinterpret_cast<float4 *>(red);
@@ -448,74 +445,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                     return make_float2(sg, sh);
                 }
             };
-            // Both sums of two coordinates at once (identical, bit for bit, to
-            // two reduce() calls).
-            auto reduce2 = [&](float4 v) -> float4 {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    v.x += __shfl_xor_sync(kFull, v.x, o);
-                    v.y += __shfl_xor_sync(kFull, v.y, o);
-                    v.z += __shfl_xor_sync(kFull, v.z, o);
-                    v.w += __shfl_xor_sync(kFull, v.w, o);
-                }
-                if constexpr (kCta) {
-                    float4 *rb = red4 + parity * kNW;
-                    if (lane == 0) rb[warp_in_block] = v;
-                    __syncthreads();
-                    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int w = 0; w < kNW; ++w) {
-                        const float4 u = rb[w];
-                        t.x += u.x;
-                        t.y += u.y;
-                        t.z += u.z;
-                        t.w += u.w;
-                    }
-                    parity ^= 1;
-                    return t;
-                } else {
-                    return v;
-                }
-            };
-            // Coordinates at zero whose derivative points outward stay at zero
-            // and change nothing; two such consecutive coordinates are
-            // evaluated together, and the second evaluation is used only if
-            // the first coordinate did not move (then it is exactly what a
-            // sequential evaluation would give).
 #pragma unroll
             for (int i = 0; i < D - 1; ++i) issue(i);
-            int issued = D - 1;
-            for (int kk = 0; kk < r;) {
-                while (issued < kk + D) issue(issued++);
-                const int k = perm[kk];
-                const bool pair = kk + 1 < r && x_init[k] == 0.f && x_init[perm[kk + 1]] == 0.f;
-                float2 first1 = make_float2(0.f, 0.f);
-                bool has0 = false;
-                float2 first0 = make_float2(0.f, 0.f);
-                if (pair) {
-                    cp_async_wait<D - 2>();
-                    const float *a0 = myring + (kk % D) * K * NT;
-                    const float *a1 = myring + ((kk + 1) % D) * K * NT;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int s = 0; s < K; ++s) {
-                        if (s < ks) {
-                            const float av0 = a0[s * NT], av1 = a1[s * NT];
-                            v.x = fmaf(wr[s], av0, v.x);
-                            v.y = fmaf(qr[s] * av0, av0, v.y);
-                            v.z = fmaf(wr[s], av1, v.z);
-                            v.w = fmaf(qr[s] * av1, av1, v.w);
-                        }
-                    }
-                    v = reduce2(v);
-                    has0 = true;
-                    first0 = make_float2(v.x, v.y);
-                    first1 = make_float2(v.z, v.w);
-                } else {
-                    cp_async_wait<D - 1>();
-                }
+            for (int kk = 0; kk < r; ++kk) {
+                issue(kk + D - 1);
+                cp_async_wait<D - 1>();
                 const float *ac = myring + (kk % D) * K * NT;
-                bool moved = false;
+                const int k = perm[kk];
                 auto eval = [&]() -> float2 {
                     float sg = 0.f, sh = 0.f;
 #pragma unroll
@@ -529,7 +465,6 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                     return reduce(sg, sh);
                 };
                 auto update = [&](float d, int dc) {
-                    moved = true;
 #pragma unroll
                     for (int s = 0; s < K; ++s) {
                         if (s < ks) {
@@ -540,40 +475,8 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                         }
                     }
                 };
-                const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally, has0, first0);
+                const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
                 if (tid_g == 0) x_out[k] = xk;
-                ++kk;
-                if (pair && !moved) {
-                    // the second coordinate of the pair, from its batched evaluation
-                    const float *ac1 = myring + (kk % D) * K * NT;
-                    const int k1 = perm[kk];
-                    auto eval1 = [&]() -> float2 {
-                        float sg = 0.f, sh = 0.f;
-#pragma unroll
-                        for (int s = 0; s < K; ++s) {
-                            if (s < ks) {
-                                const float av = ac1[s * NT];
-                                sg = fmaf(wr[s], av, sg);
-                                sh = fmaf(qr[s] * av, av, sh);
-                            }
-                        }
-                        return reduce(sg, sh);
-                    };
-                    auto update1 = [&](float d, int dc) {
-#pragma unroll
-                        for (int s = 0; s < K; ++s) {
-                            if (s < ks) {
-                                xr[s] = step_x(xr[s], ac1[s * NT], d, dc, cr[s]);
-                                const float ri = recip(xr[s] + eps_div);
-                                wr[s] = vr[s] * ri;
-                                qr[s] = wr[s] * ri;
-                            }
-                        }
-                    };
-                    const float xk1 = newton_coordinate(a, x_init[k1], a.sumA[k1], eval1, update1, tally, true, first1);
-                    if (tid_g == 0) x_out[k1] = xk1;
-                    ++kk;
-                }
             }
             cp_async_wait<0>();
         };
@@ -1833,26 +1736,33 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
         sparse = c->density[side] < 0.5;
     }
     c->used_sparse[side] = sparse ? 1 : 0;
+    // Buckets run one after another on the context stream. (Running them
+    // concurrently on side streams, so that one bucket's tail overlaps the
+    // next one's work, was measured slower: 139 vs 133 ms per step on the
+    // large corpus; the concurrent persistent kernels contend for L2.)
+    std::vector<Bucket> &plan = sparse ? c->plan_sparse[side] : c->plan[side];
     int qi = 0;
-    for (auto &b : sparse ? c->plan_sparse[side] : c->plan[side]) {
+    for (auto &b : plan) {
+        cudaStream_t st = c->stream;
         a.units = b.d_units;
         a.count = b.count;
         a.queue = c->queues + side * 16 + qi++;
         a.slot_floats = b.slot_floats;
         a.lcap = b.lcap;
-        if (!cuda_ok(c, cudaMemsetAsync(a.queue, 0, sizeof(int32_t), c->stream), "reset queue"))
+        a.scratch = c->scratch;
+        if (!cuda_ok(c, cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st), "reset queue"))
             return NMFKL_ECUDA;
         void *args[] = {&a};
         const int tok = timer_begin(c, bucket_name(b));
         cudaError_t e;
         if (b.sparse) {
-            e = cudaLaunchKernel(kSparseKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, c->stream);
+            e = cudaLaunchKernel(kSparseKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
         } else if (b.cl > 1) {
             cudaLaunchConfig_t cfg{};
             cfg.gridDim = dim3(b.grid);
             cfg.blockDim = dim3(b.block);
             cfg.dynamicSmemBytes = b.smem;
-            cfg.stream = c->stream;
+            cfg.stream = st;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
             attr[0].val.clusterDim.x = b.cl;
@@ -1862,7 +1772,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
             cfg.numAttrs = 1;
             e = cudaLaunchKernelExC(&cfg, kKinds[b.kind].fn, args);
         } else {
-            e = cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, c->stream);
+            e = cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
         }
         timer_end(c, tok);
         if (!cuda_ok(c, e, bucket_name(b))) return NMFKL_ECUDA;
