@@ -1020,7 +1020,7 @@ __host__ __device__ inline SparseLayout sparse_layout(int r, int ldr, int nt, in
     g.tm_off = off;
     off = align16(off + 2 * ns);
     g.lbuf_off = off;
-    if (scap == 0) off = align16(off + 2 * (size_t)(nt / 32) * kSparseCapW * sizeof(int2));
+    if (scap == 0) off = align16(off + 3 * (size_t)(nt / 32) * kSparseCapW * sizeof(int2));
     g.bytes = off;
     return g;
 }
@@ -1039,12 +1039,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-template <int NT>
+// Register budgets: two blocks of eight warps (128 registers) for warp
+// groups. (85 registers and three blocks for the slot-state warp groups was
+// measured slower: 153 vs 133 ms per step.)
+template <int NT, bool kSmemState>
 __host__ __device__ constexpr int sparse_min_blocks() {
     return NT == 32 ? 2 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
 }
 template <int NT, bool kSmemState>
-__global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) sparse_kernel(HalfArgs a) {
+__global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kSmemState>())) sparse_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
     constexpr int kNW = NT / 32;
@@ -1076,18 +1079,21 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
         wq = reinterpret_cast<float2 *>(gs + lay.wq_off);
         tm = reinterpret_cast<uint16_t *>(gs + lay.tm_off);
     } else {
+        // interleaved (x_p, v_p, w_p, q_p) per nonzero: one 16-byte piece, so a
+        // prefetch of the piece brings everything a later access to p needs
         xv = reinterpret_cast<float2 *>(slot + 2 * (int64_t)r * lcap);
-        wq = xv + lcap + 1;
-        tm = reinterpret_cast<uint16_t *>(wq + lcap + 1);
+        wq = xv + 1;
+        tm = reinterpret_cast<uint16_t *>(xv + 2 * ((int64_t)lcap + 1));
     }
+    constexpr int XS = kSmemState ? 1 : 2;  // float2 stride of xv and wq
     __shared__ int s_q;
     const float eps_div = a.eps_div;
     const int count = a.count_dev ? *a.count_dev : a.count;
     Tally tally;
     int parity = 0;
     if (tid_g == 0) {  // the dummy entry's state: zero, and it stays zero
-        xv[lcap] = make_float2(0.f, 0.f);
-        wq[lcap] = make_float2(0.f, 0.f);
+        xv[XS * (lcap)] = make_float2(0.f, 0.f);
+        wq[XS * (lcap)] = make_float2(0.f, 0.f);
         tm[lcap] = 0;
     }
 
@@ -1203,8 +1209,8 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
             if (valid) {
                 const float xl = terms == 0 ? 0.f : acc;
                 const float ri = recip(xl + eps_div);
-                xv[p] = make_float2(xl, v);
-                wq[p] = make_float2(v * ri, v * ri * ri);
+                xv[XS * (p)] = make_float2(xl, v);
+                wq[XS * (p)] = make_float2(v * ri, v * ri * ri);
                 tm[p] = (uint16_t)terms;
             }
             __syncwarp();
@@ -1255,7 +1261,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
                 auto eval = [&]() -> float2 {
                     float sg = 0.f, sh = 0.f;
                     auto acc = [&](int p, float av) {
-                        const float2 st = wq[p];
+                        const float2 st = wq[XS * (p)];
                         sg = fmaf(st.x, av, sg);
                         sh = fmaf(st.y * av, av, sh);
                     };
@@ -1267,13 +1273,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
                 };
                 auto update = [&](float d, int dc) {
                     auto upd = [&](int p, float av) {
-                        const float2 st = xv[p];
+                        const float2 st = xv[XS * (p)];
                         int terms = dc != 0 ? (int)tm[p] : 0;
                         const float xn = step_x(st.x, av, d, dc, terms);
                         if (dc != 0) tm[p] = (uint16_t)terms;
                         const float ri = recip(xn + eps_div);
-                        xv[p].x = xn;
-                        wq[p] = make_float2(st.y * ri, st.y * ri * ri);
+                        xv[XS * (p)].x = xn;
+                        wq[XS * (p)] = make_float2(st.y * ri, st.y * ri * ri);
                     };
 #pragma unroll
                     for (int t = 0; t < E; ++t)
@@ -1299,27 +1305,41 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
             // coordinate into shared memory (cp.async, up to kSparseCapW
             // entries) while it works on the current one, and issues the state
             // loads eight at a time.
-            int2 *lbuf = reinterpret_cast<int2 *>(gs + lay.lbuf_off) + (size_t)w * 2 * kSparseCapW;
+            // Lists are staged two coordinates ahead; once the next one has
+            // landed, the 16-byte state pieces of its entries are prefetched
+            // into L1, so the next evaluation finds them there (stores of the
+            // current coordinate to the same pieces reach L1 too).
+            int2 *lbuf = reinterpret_cast<int2 *>(gs + lay.lbuf_off) + (size_t)w * 3 * kSparseCapW;
             auto stage_list = [&](int pos) {
                 if (pos < r) {
                     const int k = perm[pos];
                     const int cn = min(mycnt[k], kSparseCapW);
                     const int2 *src = mylists + (int64_t)k * LW;
-                    int2 *dst = lbuf + (pos & 1) * kSparseCapW;
+                    int2 *dst = lbuf + (pos % 3) * kSparseCapW;
                     for (int c = lane; 2 * c < cn; c += 32) cp_async16(dst + 2 * c, src + 2 * c);
                 }
                 cp_async_commit();
             };
+            auto prefetch_state = [&](int pos) {
+                if (pos < r) {
+                    const int cn = min(mycnt[perm[pos]], kSparseCapW);
+                    const int2 *lb = lbuf + (pos % 3) * kSparseCapW;
+                    for (int j = lane; j < cn; j += 32)
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(xv + XS * lb[j].x));
+                }
+            };
             constexpr int kU = 8;
             stage_list(0);
+            stage_list(1);
             for (int kk = 0; kk < r; ++kk) {
-                stage_list(kk + 1);
+                stage_list(kk + 2);
                 cp_async_wait<1>();
                 __syncwarp();
+                prefetch_state(kk + 1);
                 const int k = perm[kk];
                 const int cn = mycnt[k];
                 const int2 *lk = mylists + (int64_t)k * LW;
-                const int2 *lb = lbuf + (kk & 1) * kSparseCapW;
+                const int2 *lb = lbuf + (kk % 3) * kSparseCapW;
                 auto entry = [&](int j) -> int2 { return j < kSparseCapW ? lb[j] : __ldcg(lk + j); };
                 auto eval = [&]() -> float2 {
                     float sg = 0.f, sh = 0.f;
@@ -1329,7 +1349,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
 #pragma unroll
                         for (int t = 0; t < kU; ++t) e[t] = j0 + 32 * t < cn ? entry(j0 + 32 * t) : make_int2(0, 0);
 #pragma unroll
-                        for (int t = 0; t < kU; ++t) st[t] = j0 + 32 * t < cn ? wq[e[t].x] : make_float2(0.f, 0.f);
+                        for (int t = 0; t < kU; ++t) st[t] = j0 + 32 * t < cn ? wq[XS * (e[t].x)] : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int t = 0; t < kU; ++t) {
                             const float av = __int_as_float(e[t].y);
@@ -1346,7 +1366,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
 #pragma unroll
                         for (int t = 0; t < kU; ++t) e[t] = j0 + 32 * t < cn ? entry(j0 + 32 * t) : make_int2(0, 0);
 #pragma unroll
-                        for (int t = 0; t < kU; ++t) st[t] = j0 + 32 * t < cn ? xv[e[t].x] : make_float2(0.f, 0.f);
+                        for (int t = 0; t < kU; ++t) st[t] = j0 + 32 * t < cn ? xv[XS * (e[t].x)] : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int t = 0; t < kU; ++t) {
                             if (j0 + 32 * t < cn) {
@@ -1355,8 +1375,8 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
                                 const float xn = step_x(st[t].x, __int_as_float(e[t].y), d, dc, terms);
                                 if (dc != 0) tm[p] = (uint16_t)terms;
                                 const float ri = recip(xn + eps_div);
-                                xv[p].x = xn;
-                                wq[p] = make_float2(st[t].y * ri, st[t].y * ri * ri);
+                                xv[XS * (p)].x = xn;
+                                wq[XS * (p)] = make_float2(st[t].y * ri, st[t].y * ri * ri);
                             }
                         }
                     }
@@ -1374,7 +1394,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, sparse_min_blocks<NT>()) 
             for (int c = w; c < nchunks; c += kNW) {
                 const int p = 32 * c + lane;
                 if (p < L) {
-                    const float2 s = xv[p];
+                    const float2 s = xv[XS * (p)];
                     t += kl_term(s.y, s.x, eps_div);
                 }
             }
@@ -1483,6 +1503,7 @@ struct SparseKind {
 // in the slot beyond), one 512-thread CTA per unit past that.
 const SparseKind kSparseKinds[] = {
     {(const void *)sparse_kernel<32, true>, 32, 512, true, 0, "sparse_warp"},
+    {(const void *)sparse_kernel<32, true>, 32, 1024, true, 0, "sparse_warp_1k"},
     {(const void *)sparse_kernel<32, false>, 32, 2048, false, 0, "sparse_warp_g2k"},
     {(const void *)sparse_kernel<32, false>, 32, 8192, false, 8, "sparse_warp_g8k"},
     {(const void *)sparse_kernel<512, false>, 512, 0, false, 0, "sparse_giant"},
@@ -1551,8 +1572,18 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
         const size_t gbytes = sparse_layout(r, ldr, sk.nt, smem_state ? b.lcap : 0).bytes;
         int gpb = 1;
         if (!cta) {
-            gpb = 8;
-            while (gpb > 1 && gbytes * gpb > (size_t)optin) --gpb;
+            // warps per block: the most resident warps per SM that shared memory allows
+            int sm_bytes = 0;
+            cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
+            int best = 0;
+            for (int g = 8; g >= 1; --g) {
+                if (gbytes * g > (size_t)optin) continue;
+                const int blocks = std::min(2, (int)((size_t)sm_bytes / (gbytes * g + 1024)));
+                if (blocks * g > best) {
+                    best = blocks * g;
+                    gpb = g;
+                }
+            }
         }
         b.block = cta ? sk.nt : 32 * gpb;
         b.smem = gbytes * gpb;
