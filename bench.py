@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--docs", type=int, default=10_000, help="fold-in: documents per batch")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
     ap.add_argument("--r", type=int, default=100)
+    ap.add_argument("--list-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="coordinate loop: 0 chosen per half from the density, 1 dense tile, 2 sparse lists")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -267,7 +269,7 @@ def run_ours(args):
             pg.barrier()
         torch.cuda.synchronize()
 
-    model = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local)
+    model = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local, list_mode=args.list_mode)
     model.set_data(V)
     model.init()
     sweep = 0
@@ -382,7 +384,7 @@ def e2e_run(args, V, nk, torch, local, barrier, pg):
     r = args.r
     barrier()
     t0 = time.perf_counter()
-    m = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local)
+    m = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local, list_mode=args.list_mode)
     m.set_data(nnz=V.nnz, **pinned)
     m.init()
     for s in range(args.steps):

@@ -92,12 +92,13 @@ __device__ __forceinline__ void fisher_yates(uint8_t *perm, const uint64_t *word
     }
 }
 
-// The r-1 Philox words of a unit's order, generated by the 32 lanes of a warp.
+// The r-1 Philox words of a unit's order, generated by `nlanes` lanes.
 __device__ __forceinline__ void ids_words_warp(uint64_t *words, int r, int64_t unit, int64_t sweep,
-                                               int side, int perm_mode, uint64_t seed, int lane) {
+                                               int side, int perm_mode, uint64_t seed, int lane,
+                                               int nlanes = 32) {
     const int nw = r - 1;
     const int nblk = (nw + 3) / 4;
-    for (int b = lane; b < nblk; b += 32) {
+    for (int b = lane; b < nblk; b += nlanes) {
         uint64_t c[4];
         ids_counter(c, (uint64_t)b, unit, sweep, side, perm_mode);
         philox4x64_10(c, seed, kKeyIds);
@@ -1046,18 +1047,26 @@ template <int NT, bool kSmemState>
 __host__ __device__ constexpr int sparse_min_blocks() {
     return NT == 32 ? 2 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
 }
-template <int NT, bool kSmemState>
+// G < 32: sub-warp groups, 32/G units per warp, each on G lanes (shuffles,
+// ballots and barriers then name only the group's lanes).
+template <int NT, bool kSmemState, int G = 32>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kSmemState>())) sparse_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
+    static_assert(G == 32 || !kCta, "sub-warp groups are warp-level");
     constexpr int kNW = NT / 32;
     constexpr int E = kSparseE;
+    constexpr int CH = kCta ? 32 : G;   // lanes per chunk of nonzeros (a warp, or the group)
+    constexpr int GS = kCta ? NT : G;   // threads per group
     const int lane = threadIdx.x & 31;
+    const int glane = lane & (CH - 1);
+    const int gbase = lane & ~(CH - 1);
+    const unsigned gmask = CH == 32 ? kFull : (((1u << CH) - 1u) << gbase);
     const int warp_in_block = threadIdx.x >> 5;
-    const int group_in_block = kCta ? 0 : warp_in_block;
-    const int groups_per_block = kCta ? 1 : (int)(blockDim.x >> 5);
+    const int group_in_block = kCta ? 0 : (int)(threadIdx.x / G);
+    const int groups_per_block = kCta ? 1 : (int)(blockDim.x / G);
     const int w = kCta ? warp_in_block : 0;
-    const int tid_g = kCta ? (int)threadIdx.x : lane;
+    const int tid_g = kCta ? (int)threadIdx.x : glane;
     const int group_global = blockIdx.x * groups_per_block + group_in_block;
 
     const int r = a.r, ldr = a.ldr, lcap = a.lcap, nf4 = ldr >> 2;
@@ -1098,13 +1107,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
     }
 
     auto group_sync = [&]() {
-        if constexpr (kCta) __syncthreads(); else __syncwarp();
+        if constexpr (kCta) __syncthreads(); else __syncwarp(gmask);
     };
     auto reduce = [&](float sg, float sh) -> float2 {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sg += __shfl_xor_sync(kFull, sg, o);
-            sh += __shfl_xor_sync(kFull, sh, o);
+        for (int o = CH / 2; o > 0; o >>= 1) {
+            sg += __shfl_xor_sync(gmask, sg, o);
+            sh += __shfl_xor_sync(gmask, sh, o);
         }
         if constexpr (kCta) {
             float2 *rb = red + parity * kNW;
@@ -1132,10 +1141,10 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             __syncthreads();
             qi = s_q;
         } else {
-            __syncwarp();
+            __syncwarp(gmask);
             int q = 0;
-            if (lane == 0) q = atomicAdd(a.queue, 1);
-            qi = __shfl_sync(kFull, q, 0);
+            if (glane == 0) q = atomicAdd(a.queue, 1);
+            qi = __shfl_sync(gmask, q, gbase);
         }
         if (qi >= count) break;
         const int64_t u = a.units[qi];
@@ -1146,21 +1155,21 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             if (tid_g == 0) atomicOr(a.err, 4);
             continue;
         }
-        for (int k = tid_g; k < ldr; k += NT) {
+        for (int k = tid_g; k < ldr; k += GS) {
             const float xk = a.X[u * ldr + k];
             x_init[k] = xk;
             x_out[k] = xk;
         }
-        for (int k = lane; k < ldr; k += 32) mycnt[k] = 0;
+        for (int k = glane; k < ldr; k += CH) mycnt[k] = 0;
         group_sync();
 
         // ---- stage: x_p, the state, and this warp's lists
-        const int nchunks = (L + 31) >> 5;
+        const int nchunks = (L + CH - 1) / CH;
         const float4 *x4 = reinterpret_cast<const float4 *>(x_init);
         int4 *cnt4 = reinterpret_cast<int4 *>(mycnt);
-        const unsigned lt = lanemask_lt();
+        const unsigned lt = lanemask_lt() & gmask;
         for (int c = w; c < nchunks; c += kNW) {
-            const int p = 32 * c + lane;
+            const int p = CH * c + glane;
             const bool valid = p < L;
             int idx = 0;
             float v = 0.f;
@@ -1191,16 +1200,16 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                         terms += (av.x > 0.f && xk.x > 0.f) + (av.y > 0.f && xk.y > 0.f) +
                                  (av.z > 0.f && xk.z > 0.f) + (av.w > 0.f && xk.w > 0.f);
                         // padding columns (k >= r) hold 0 and never enter a list
-                        const unsigned m0 = __ballot_sync(kFull, av.x > 0.f);
-                        const unsigned m1 = __ballot_sync(kFull, av.y > 0.f);
-                        const unsigned m2 = __ballot_sync(kFull, av.z > 0.f);
-                        const unsigned m3 = __ballot_sync(kFull, av.w > 0.f);
+                        const unsigned m0 = __ballot_sync(gmask, av.x > 0.f);
+                        const unsigned m1 = __ballot_sync(gmask, av.y > 0.f);
+                        const unsigned m2 = __ballot_sync(gmask, av.z > 0.f);
+                        const unsigned m3 = __ballot_sync(gmask, av.w > 0.f);
                         int2 *l0 = mylists + (int64_t)(4 * f) * LW;
                         if (av.x > 0.f) l0[c4.x + __popc(m0 & lt)] = make_int2(p, __float_as_int(av.x));
                         if (av.y > 0.f) l0[LW + c4.y + __popc(m1 & lt)] = make_int2(p, __float_as_int(av.y));
                         if (av.z > 0.f) l0[2 * LW + c4.z + __popc(m2 & lt)] = make_int2(p, __float_as_int(av.z));
                         if (av.w > 0.f) l0[3 * LW + c4.w + __popc(m3 & lt)] = make_int2(p, __float_as_int(av.w));
-                        if (lane == 0)
+                        if (glane == 0)
                             cnt4[f] = make_int4(c4.x + __popc(m0), c4.y + __popc(m1), c4.z + __popc(m2),
                                                 c4.w + __popc(m3));
                     }
@@ -1213,13 +1222,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                 wq[XS * (p)] = make_float2(v * ri, v * ri * ri);
                 tm[p] = (uint16_t)terms;
             }
-            __syncwarp();
+            __syncwarp(gmask);
         }
         if (w == 0) {
-            ids_words_warp(words, r, perm_unit, a.sweep, a.side, a.perm_mode, a.seed, lane);
-            __syncwarp();
-            if (lane == 0) fisher_yates(perm, words, r);
-            __syncwarp();
+            ids_words_warp(words, r, perm_unit, a.sweep, a.side, a.perm_mode, a.seed, glane, CH);
+            __syncwarp(gmask);
+            if (glane == 0) fisher_yates(perm, words, r);
+            __syncwarp(gmask);
         }
         group_sync();
 
@@ -1239,20 +1248,20 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                     const int2 *lk = mylists + (int64_t)k * LW;
 #pragma unroll
                     for (int t = 0; t < E; ++t) {
-                        const int j = lane + 32 * t;
+                        const int j = glane + CH * t;
                         dst[t] = j < cn ? __ldcg(lk + j) : make_int2(0, 0);
                     }
                 }
             };
             // entries beyond the prefetched ones, four loads in flight per lane
             auto for_rest = [&](const int2 *lk, int cn, auto &&body) {
-                for (int j0 = lane + 32 * E; j0 < cn; j0 += 128) {
+                for (int j0 = glane + CH * E; j0 < cn; j0 += 4 * CH) {
                     int2 e[4];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) e[t] = j0 + 32 * t < cn ? __ldcg(lk + j0 + 32 * t) : make_int2(0, 0);
+                    for (int t = 0; t < 4; ++t) e[t] = j0 + CH * t < cn ? __ldcg(lk + j0 + CH * t) : make_int2(0, 0);
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
-                        if (j0 + 32 * t < cn) body(e[t].x, __int_as_float(e[t].y));
+                        if (j0 + CH * t < cn) body(e[t].x, __int_as_float(e[t].y));
                 }
             };
             auto coordinate = [&](int kk, int2 (&cur)[E], int cn) {
@@ -1267,7 +1276,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                     };
 #pragma unroll
                     for (int t = 0; t < E; ++t)
-                        if (lane + 32 * t < cn) acc(cur[t].x, __int_as_float(cur[t].y));
+                        if (glane + CH * t < cn) acc(cur[t].x, __int_as_float(cur[t].y));
                     for_rest(lk, cn, acc);
                     return reduce(sg, sh);
                 };
@@ -1283,10 +1292,10 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                     };
 #pragma unroll
                     for (int t = 0; t < E; ++t)
-                        if (lane + 32 * t < cn) upd(cur[t].x, __int_as_float(cur[t].y));
+                        if (glane + CH * t < cn) upd(cur[t].x, __int_as_float(cur[t].y));
                     for_rest(lk, cn, upd);
                     // the next evaluation may read these entries from other lanes
-                    __syncwarp();
+                    __syncwarp(gmask);
                 };
                 const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
                 if (tid_g == 0) x_out[k] = xk;
@@ -1316,7 +1325,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                     const int cn = min(mycnt[k], kSparseCapW);
                     const int2 *src = mylists + (int64_t)k * LW;
                     int2 *dst = lbuf + (pos % 3) * kSparseCapW;
-                    for (int c = lane; 2 * c < cn; c += 32) cp_async16(dst + 2 * c, src + 2 * c);
+                    for (int c = glane; 2 * c < cn; c += CH) cp_async16(dst + 2 * c, src + 2 * c);
                 }
                 cp_async_commit();
             };
@@ -1324,7 +1333,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                 if (pos < r) {
                     const int cn = min(mycnt[perm[pos]], kSparseCapW);
                     const int2 *lb = lbuf + (pos % 3) * kSparseCapW;
-                    for (int j = lane; j < cn; j += 32)
+                    for (int j = glane; j < cn; j += CH)
                         asm volatile("prefetch.global.L1 [%0];" ::"l"(xv + XS * lb[j].x));
                 }
             };
@@ -1334,7 +1343,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             for (int kk = 0; kk < r; ++kk) {
                 stage_list(kk + 2);
                 cp_async_wait<1>();
-                __syncwarp();
+                __syncwarp(gmask);
                 prefetch_state(kk + 1);
                 const int k = perm[kk];
                 const int cn = mycnt[k];
@@ -1343,13 +1352,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                 auto entry = [&](int j) -> int2 { return j < kSparseCapW ? lb[j] : __ldcg(lk + j); };
                 auto eval = [&]() -> float2 {
                     float sg = 0.f, sh = 0.f;
-                    for (int j0 = lane; j0 < cn; j0 += 32 * kU) {
+                    for (int j0 = glane; j0 < cn; j0 += CH * kU) {
                         int2 e[kU];
                         float2 st[kU];
 #pragma unroll
-                        for (int t = 0; t < kU; ++t) e[t] = j0 + 32 * t < cn ? entry(j0 + 32 * t) : make_int2(0, 0);
+                        for (int t = 0; t < kU; ++t) e[t] = j0 + CH * t < cn ? entry(j0 + CH * t) : make_int2(0, 0);
 #pragma unroll
-                        for (int t = 0; t < kU; ++t) st[t] = j0 + 32 * t < cn ? wq[XS * (e[t].x)] : make_float2(0.f, 0.f);
+                        for (int t = 0; t < kU; ++t) st[t] = j0 + CH * t < cn ? wq[XS * (e[t].x)] : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int t = 0; t < kU; ++t) {
                             const float av = __int_as_float(e[t].y);
@@ -1360,16 +1369,16 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                     return reduce(sg, sh);
                 };
                 auto update = [&](float d, int dc) {
-                    for (int j0 = lane; j0 < cn; j0 += 32 * kU) {
+                    for (int j0 = glane; j0 < cn; j0 += CH * kU) {
                         int2 e[kU];
                         float2 st[kU];
 #pragma unroll
-                        for (int t = 0; t < kU; ++t) e[t] = j0 + 32 * t < cn ? entry(j0 + 32 * t) : make_int2(0, 0);
+                        for (int t = 0; t < kU; ++t) e[t] = j0 + CH * t < cn ? entry(j0 + CH * t) : make_int2(0, 0);
 #pragma unroll
-                        for (int t = 0; t < kU; ++t) st[t] = j0 + 32 * t < cn ? xv[XS * (e[t].x)] : make_float2(0.f, 0.f);
+                        for (int t = 0; t < kU; ++t) st[t] = j0 + CH * t < cn ? xv[XS * (e[t].x)] : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int t = 0; t < kU; ++t) {
-                            if (j0 + 32 * t < cn) {
+                            if (j0 + CH * t < cn) {
                                 const int p = e[t].x;
                                 int terms = dc != 0 ? (int)tm[p] : 0;
                                 const float xn = step_x(st[t].x, __int_as_float(e[t].y), d, dc, terms);
@@ -1380,25 +1389,27 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                             }
                         }
                     }
-                    __syncwarp();
+                    __syncwarp(gmask);
                 };
                 const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
                 if (tid_g == 0) x_out[k] = xk;
                 // the buffer just read is refilled two coordinates on
-                __syncwarp();
+                __syncwarp(gmask);
             }
             cp_async_wait<0>();
         }
         if (a.unit_obj) {
             float t = 0.f;
             for (int c = w; c < nchunks; c += kNW) {
-                const int p = 32 * c + lane;
+                const int p = CH * c + glane;
                 if (p < L) {
                     const float2 s = xv[XS * (p)];
                     t += kl_term(s.y, s.x, eps_div);
                 }
             }
-            double dt = warp_sum_d((double)t);
+            double dt = (double)t;
+#pragma unroll
+            for (int o = CH / 2; o > 0; o >>= 1) dt += __shfl_xor_sync(gmask, dt, o);
             if constexpr (kCta) {
                 double *rd = reinterpret_cast<double *>(red + parity * kNW);
                 if (lane == 0) rd[warp_in_block] = dt;
@@ -1416,9 +1427,9 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
         for (int k = 0; k < r; ++k) {
             const int lines = (mycnt[k] * 8) / 128;
             const char *l0 = reinterpret_cast<const char *>(mylists + (int64_t)k * LW);
-            for (int i = lane; i < lines; i += 32) asm volatile("discard.global.L2 [%0], 128;" ::"l"(l0 + 128 * i) : "memory");
+            for (int i = glane; i < lines; i += CH) asm volatile("discard.global.L2 [%0], 128;" ::"l"(l0 + 128 * i) : "memory");
         }
-        for (int k = tid_g; k < r; k += NT) {
+        for (int k = tid_g; k < r; k += GS) {
             const float xk = x_out[k];
             if (!(xk == xk)) atomicOr(a.err, 1);
             a.X[u * ldr + k] = xk;
@@ -1493,20 +1504,24 @@ int active_clusters(int cl, size_t smem) {
 
 struct SparseKind {
     const void *fn;
-    int nt;          // threads per group (32: warp groups, several per block)
+    int nt;          // threads per CTA group, or 32 for warp-level groups
+    int g;           // lanes per warp-level group (8, 16 or 32)
     int cap;         // longest unit (nonzeros) of the class; 0: no limit
     bool smem;       // per-nonzero state in shared memory (else in the slot)
     int max_groups;  // resident groups per SM at most (0: as many as fit)
     const char *name;
 };
-// One warp per unit up to 8,192 nonzeros (state in shared memory up to 512,
-// in the slot beyond), one 512-thread CTA per unit past that.
+// Short units on 8 or 16 lanes (four or two units per warp), one warp per
+// unit up to 8,192 nonzeros (state in shared memory up to 1,024, in the slot
+// beyond), one 512-thread CTA per unit past that.
 const SparseKind kSparseKinds[] = {
-    {(const void *)sparse_kernel<32, true>, 32, 512, true, 0, "sparse_warp"},
-    {(const void *)sparse_kernel<32, true>, 32, 1024, true, 0, "sparse_warp_1k"},
-    {(const void *)sparse_kernel<32, false>, 32, 2048, false, 0, "sparse_warp_g2k"},
-    {(const void *)sparse_kernel<32, false>, 32, 8192, false, 8, "sparse_warp_g8k"},
-    {(const void *)sparse_kernel<512, false>, 512, 0, false, 0, "sparse_giant"},
+    {(const void *)sparse_kernel<32, true, 8>, 32, 8, 64, true, 0, "sparse_g8"},
+    {(const void *)sparse_kernel<32, true, 16>, 32, 16, 128, true, 0, "sparse_g16"},
+    {(const void *)sparse_kernel<32, true>, 32, 32, 512, true, 0, "sparse_warp"},
+    {(const void *)sparse_kernel<32, true>, 32, 32, 1024, true, 0, "sparse_warp_1k"},
+    {(const void *)sparse_kernel<32, false>, 32, 32, 2048, false, 0, "sparse_warp_g2k"},
+    {(const void *)sparse_kernel<32, false>, 32, 32, 8192, false, 8, "sparse_warp_g8k"},
+    {(const void *)sparse_kernel<512, false>, 512, 32, 0, false, 0, "sparse_giant"},
 };
 constexpr int kNumSparseKinds = sizeof(kSparseKinds) / sizeof(kSparseKinds[0]);
 
@@ -1567,7 +1582,7 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
         b.count = (int32_t)lst.size();
         b.max_len = maxlen[kind];
         b.nnz = nnz[kind];
-        const int64_t chunk = 32 * (int64_t)(sk.nt / 32);
+        const int64_t chunk = cta ? 32 * (int64_t)(sk.nt / 32) : sk.g;
         b.lcap = (int32_t)std::max<int64_t>(chunk, (b.max_len + chunk - 1) / chunk * chunk);
         const size_t gbytes = sparse_layout(r, ldr, sk.nt, smem_state ? b.lcap : 0).bytes;
         int gpb = 1;
@@ -1576,7 +1591,7 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
             int sm_bytes = 0;
             cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
             int best = 0;
-            for (int g = 8; g >= 1; --g) {
+            for (int g = 256 / sk.g; g >= 1; --g) {
                 if (gbytes * g > (size_t)optin) continue;
                 const int blocks = std::min(2, (int)((size_t)sm_bytes / (gbytes * g + 1024)));
                 if (blocks * g > best) {
@@ -1585,7 +1600,7 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
                 }
             }
         }
-        b.block = cta ? sk.nt : 32 * gpb;
+        b.block = cta ? sk.nt : sk.g * gpb;
         b.smem = gbytes * gpb;
         if (b.smem > (size_t)optin) {
             c->err = "sparse plan: shared memory exceeds the device limit";
