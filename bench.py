@@ -278,6 +278,10 @@ def run_ours(args):
         sweep += 1
     model.counters(reset=True)
     model.kernel_times(reset=True)
+    # per-kernel CUDA events on the library's stream (the buckets run one after
+    # another there anyway) give the breakdown and the launch count of the
+    # timed steps
+    model.set_timing(True)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -297,20 +301,17 @@ def run_ours(args):
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
     counters = model.counters(reset=True)
-    # per-kernel durations: one more step with every launch bracketed by events
-    # (the library then runs the buckets one after another on its stream), not
-    # part of the timed region above
-    model.set_timing(True)
-    model.step(sweep)
     model.set_timing(False)
     times = model.kernel_times(reset=True)
-    plan = [b for b in model.plan() if b["ran_last"]]  # the buckets that step ran
+    plan_all = model.plan()  # both plans (dense tile, sparse lists) of both halves
     value = ws * U * args.steps / (ms / 1e3)
 
-    # roofline of the dominant kernel family
+    # roofline of the dominant kernel family: its algorithmic bytes per launch
+    # (the mean over the buckets of that kernel, one per half it serves) over
+    # its mean launch time in the timed steps
     peak, peak_kind = measured_peak_hbm()
     fam = {}
-    for b in plan:
+    for b in plan_all:
         units = b["count"]
         e = fam.setdefault(b["kernel"], {"bytes": 0, "nnz": 0, "units": 0})
         e["bytes"] += algorithmic_bytes(b["nnz"], units, r)
@@ -320,12 +321,11 @@ def run_ours(args):
     dom = max(sweep_kernels, key=lambda k: sweep_kernels[k][1])
     launches, dom_ms = sweep_kernels[dom]
     per_launch_ms = dom_ms / max(launches, 1)
-    bytes_per_launch = fam[dom]["bytes"] / max(1, sum(1 for b in plan if b["kernel"] == dom))
-    # each launch handles one (half, bucket); a family may run on both halves
-    nlaunch_per_step = sum(1 for b in plan if b["kernel"] == dom)
-    bytes_per_launch = fam[dom]["bytes"] / nlaunch_per_step
+    nbuckets = sum(1 for b in plan_all if b["kernel"] == dom)
+    bytes_per_launch = fam[dom]["bytes"] / max(1, nbuckets)
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
-    step_bytes = sum(algorithmic_bytes(b["nnz"], b["count"], r) for b in plan)
+    # a step moves each half's bytes once, whichever plan runs it
+    step_bytes = sum(algorithmic_bytes(b["nnz"], b["count"], r) for b in plan_all if b["kernel"].startswith("sweep_"))
     ms_step = ms / args.steps
     traffic = ncu_traffic(dom, args.workload, r)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

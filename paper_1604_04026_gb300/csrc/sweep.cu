@@ -1048,8 +1048,10 @@ __host__ __device__ constexpr int sparse_min_blocks() {
     return NT == 32 ? 2 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
 }
 // G < 32: sub-warp groups, 32/G units per warp, each on G lanes (shuffles,
-// ballots and barriers then name only the group's lanes).
-template <int NT, bool kSmemState, int G = 32>
+// ballots and barriers then name only the group's lanes). kClass only tells
+// length classes that share the other parameters apart (one symbol per class,
+// so that profiles attribute launches to classes).
+template <int NT, bool kSmemState, int G = 32, int kClass = 0>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kSmemState>())) sparse_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
@@ -1518,9 +1520,9 @@ const SparseKind kSparseKinds[] = {
     {(const void *)sparse_kernel<32, true, 8>, 32, 8, 64, true, 0, "sparse_g8"},
     {(const void *)sparse_kernel<32, true, 16>, 32, 16, 128, true, 0, "sparse_g16"},
     {(const void *)sparse_kernel<32, true>, 32, 32, 512, true, 0, "sparse_warp"},
-    {(const void *)sparse_kernel<32, true>, 32, 32, 1024, true, 0, "sparse_warp_1k"},
+    {(const void *)sparse_kernel<32, true, 32, 1>, 32, 32, 1024, true, 0, "sparse_warp_1k"},
     {(const void *)sparse_kernel<32, false>, 32, 32, 2048, false, 0, "sparse_warp_g2k"},
-    {(const void *)sparse_kernel<32, false>, 32, 32, 8192, false, 8, "sparse_warp_g8k"},
+    {(const void *)sparse_kernel<32, false, 32, 1>, 32, 32, 8192, false, 8, "sparse_warp_g8k"},
     {(const void *)sparse_kernel<512, false>, 512, 32, 0, false, 0, "sparse_giant"},
 };
 constexpr int kNumSparseKinds = sizeof(kSparseKinds) / sizeof(kSparseKinds[0]);
