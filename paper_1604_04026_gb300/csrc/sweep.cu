@@ -994,7 +994,8 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 // Warp w of the group owns the chunks of 32 nonzeros c = w, w + NW, ...; its
 // lists hold only its own nonzeros, so warps never touch each other's state.
 // ---------------------------------------------------------------------------
-constexpr int kSparseE = 4;  // list entries per lane prefetched into registers
+// list entries per lane prefetched into registers: warp groups, CTA groups
+constexpr int kSparseE = 4, kSparseECta = 8;
 
 constexpr int kSparseCapW = 256;  // list entries per warp staged in shared memory per coordinate
 
@@ -1057,7 +1058,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
     constexpr bool kCta = NT > 32;
     static_assert(G == 32 || !kCta, "sub-warp groups are warp-level");
     constexpr int kNW = NT / 32;
-    constexpr int E = kSparseE;
+    constexpr int E = kCta ? kSparseECta : kSparseE;
     constexpr int CH = kCta ? 32 : G;   // lanes per chunk of nonzeros (a warp, or the group)
     constexpr int GS = kCta ? NT : G;   // threads per group
     const int lane = threadIdx.x & 31;
@@ -1514,22 +1515,42 @@ struct SparseKind {
     const char *name;
 };
 // Short units on 8 or 16 lanes (four or two units per warp), one warp per
-// unit up to 8,192 nonzeros (state in shared memory up to 1,024, in the slot
-// beyond), one 512-thread CTA per unit past that.
+// unit up to 1,024 nonzeros, then one CTA of 128 / 256 / 512 threads per unit
+// up to 2,048 / 4,096 nonzeros / as many as its shared memory holds (about
+// 12,000 at r = 100), all with the per-nonzero state in shared memory; past
+// that one 512-thread CTA per unit with the state in the slot. A class whose
+// shared-memory layout does not fit passes its units on to the next one (at
+// r <= 256 the 128- and 256-thread layouts always fit, the 512-thread one up
+// to at least 11,264 nonzeros). One warp per unit with the state in the slot,
+// for 1,025..8,192 nonzeros, measured 9% slower per step at r = 100.
 const SparseKind kSparseKinds[] = {
     {(const void *)sparse_kernel<32, true, 8>, 32, 8, 64, true, 0, "sparse_g8"},
     {(const void *)sparse_kernel<32, true, 16>, 32, 16, 128, true, 0, "sparse_g16"},
     {(const void *)sparse_kernel<32, true>, 32, 32, 512, true, 0, "sparse_warp"},
     {(const void *)sparse_kernel<32, true, 32, 1>, 32, 32, 1024, true, 0, "sparse_warp_1k"},
-    {(const void *)sparse_kernel<32, false>, 32, 32, 2048, false, 0, "sparse_warp_g2k"},
-    {(const void *)sparse_kernel<32, false, 32, 1>, 32, 32, 8192, false, 8, "sparse_warp_g8k"},
+    {(const void *)sparse_kernel<128, true>, 128, 32, 2048, true, 0, "sparse_cta128"},
+    {(const void *)sparse_kernel<256, true>, 256, 32, 4096, true, 0, "sparse_cta256"},
+    {(const void *)sparse_kernel<512, true>, 512, 32, 16384, true, 0, "sparse_cta512"},
     {(const void *)sparse_kernel<512, false>, 512, 32, 0, false, 0, "sparse_giant"},
 };
 constexpr int kNumSparseKinds = sizeof(kSparseKinds) / sizeof(kSparseKinds[0]);
 
-int sparse_kind_for_length(int64_t L) {
-    for (int i = 0; i < kNumSparseKinds - 1; ++i)
-        if (L <= kSparseKinds[i].cap) return i;
+// Row length of a unit of L nonzeros in a group of the kind (whole chunks of
+// every warp of the group).
+int64_t sparse_lcap(const SparseKind &sk, int64_t L) {
+    const int64_t chunk = sk.nt > 32 ? sk.nt : sk.g;
+    return std::max<int64_t>(chunk, (L + chunk - 1) / chunk * chunk);
+}
+
+// The first class whose cap holds L and, for shared-memory state, whose
+// group layout fits the per-block limit.
+int sparse_kind_for_length(int64_t L, int r, int ldr, int optin) {
+    for (int i = 0; i < kNumSparseKinds - 1; ++i) {
+        const SparseKind &sk = kSparseKinds[i];
+        if (L > sk.cap) continue;
+        if (sk.smem && sparse_layout(r, ldr, sk.nt, (int)sparse_lcap(sk, L)).bytes > (size_t)optin) continue;
+        return i;
+    }
     return kNumSparseKinds - 1;
 }
 
@@ -1561,7 +1582,7 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
     std::vector<int64_t> maxlen(kNumSparseKinds, 0), nnz(kNumSparseKinds, 0);
     for (int64_t u = 0; u < units; ++u) {
         const int64_t L = ptr[u + 1] - ptr[u];
-        const int kind = sparse_kind_for_length(L);
+        const int kind = sparse_kind_for_length(L, r, ldr, optin);
         lists[kind].push_back((int32_t)u);
         maxlen[kind] = std::max(maxlen[kind], L);
         nnz[kind] += L;
@@ -1584,8 +1605,7 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
         b.count = (int32_t)lst.size();
         b.max_len = maxlen[kind];
         b.nnz = nnz[kind];
-        const int64_t chunk = cta ? 32 * (int64_t)(sk.nt / 32) : sk.g;
-        b.lcap = (int32_t)std::max<int64_t>(chunk, (b.max_len + chunk - 1) / chunk * chunk);
+        b.lcap = (int32_t)sparse_lcap(sk, b.max_len);
         const size_t gbytes = sparse_layout(r, ldr, sk.nt, smem_state ? b.lcap : 0).bytes;
         int gpb = 1;
         if (!cta) {

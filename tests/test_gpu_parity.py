@@ -31,7 +31,8 @@ pytestmark = pytest.mark.gpu
 LIST_MODES = [1, 2]
 
 BUCKET_LENGTHS = [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513,
-                  1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 12000]
+                  1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 12000,
+                  12799, 12800, 12801, 13500]
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +44,7 @@ def torch():
 
 @pytest.fixture(scope="module")
 def designed():
-    return designed_matrix(13000, 12500, BUCKET_LENGTHS, BUCKET_LENGTHS, seed=1)
+    return designed_matrix(14000, 14000, BUCKET_LENGTHS, BUCKET_LENGTHS, seed=1)
 
 
 @pytest.fixture(scope="module")
@@ -150,10 +151,25 @@ def _check_halves(V, W0, F0, Fg, Fo, Wg, Wo, F1, p, fraction=1.0, obj_rel=OBJ_RE
         assert (err <= obj_rel * scale + PROBE_FACTOR * d_dev).all(), (side, float((err / scale).max()))
 
 
+def test_designed_lengths_reach_every_list_class(designed):
+    """The designed lengths put units into every reachable sparse-list class
+    on both halves (the tight parity test above then covers each of them)."""
+    r = 16
+    W0, F0 = start(designed, r, seed=2)
+    m = model(designed, W0, F0, params(r, seed=5, list_mode=2))
+    want = {"sparse_g8", "sparse_g16", "sparse_warp", "sparse_warp_1k", "sparse_cta128", "sparse_cta256",
+            "sparse_cta512", "sparse_giant"}
+    for side in (0, 1):
+        kinds = {b["kernel"] for b in m.plan() if b["side"] == side and b["kernel"].startswith("sparse_")}
+        assert want <= kinds, (side, want - kinds)
+    m.close()
+
+
 @pytest.mark.parametrize("list_mode", LIST_MODES)
 def test_halves_tight_every_bucket(designed, list_mode):
-    """Unit lengths 0..12000 around every bucket edge (warp K=1..16, CTA,
-    clusters, giant; sparse-list warp, CTA and giant classes)."""
+    """Unit lengths 0..13500 around every bucket edge (warp K=1..16, CTA,
+    clusters, giant; sparse-list sub-warp, warp, CTA and giant classes; at
+    r = 16 the 512-thread shared-state list class ends at 12,800)."""
     V = designed
     r = 16
     W0, F0 = start(V, r, seed=2)
@@ -381,7 +397,7 @@ def test_long_rows_every_cluster_size(list_mode):
     m_ = model(V, W0, F0, p)
     kinds = {b["kernel"] for b in m_.plan() if b["side"] == 1}
     assert any(k.startswith("sweep_cluster") for k in kinds), kinds
-    assert "sparse_giant" in kinds and "sparse_warp_g8k" in kinds, kinds
+    assert "sparse_giant" in kinds and "sparse_cta512" in kinds, kinds
     m_.sweep_W(0)
     Wg = m_.get_W()
     m_.close()
