@@ -737,6 +737,16 @@ __device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
 __device__ __forceinline__ void st_cluster_u64(uint32_t addr, unsigned long long v) {
     asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
 }
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long pack_f2(float x, float y) {
+    return (static_cast<unsigned long long>(__float_as_uint(y)) << 32) | __float_as_uint(x);
+}
+__device__ __forceinline__ float2 unpack_f2(unsigned long long v) {
+    return make_float2(__uint_as_float(static_cast<unsigned>(v & 0xffffffffull)),
+                       __uint_as_float(static_cast<unsigned>(v >> 32)));
+}
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
 }
@@ -1004,7 +1014,8 @@ struct SparseLayout {
 };
 // scap: nonzeros whose state is in shared memory (0: state in the slot, and a
 // double-buffered shared copy of each warp's list for the current coordinate)
-__host__ __device__ inline SparseLayout sparse_layout(int r, int ldr, int nt, int scap) {
+// compact: shared-memory state of (x_p, v_p) and the term count only
+__host__ __device__ inline SparseLayout sparse_layout(int r, int ldr, int nt, int scap, bool compact) {
     SparseLayout g{};
     size_t off = align16(256 + 2 * (size_t)ldr * 4);  // perm | x_init | x_out
     g.words_off = off;
@@ -1018,7 +1029,7 @@ __host__ __device__ inline SparseLayout sparse_layout(int r, int ldr, int nt, in
     g.xv_off = off;
     off = align16(off + 8 * ns);
     g.wq_off = off;
-    off = align16(off + 8 * ns);
+    if (!compact) off = align16(off + 8 * ns);
     g.tm_off = off;
     off = align16(off + 2 * ns);
     g.lbuf_off = off;
@@ -1049,14 +1060,28 @@ __host__ __device__ constexpr int sparse_min_blocks() {
     return NT == 32 ? 2 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
 }
 // G < 32: sub-warp groups, 32/G units per warp, each on G lanes (shuffles,
-// ballots and barriers then name only the group's lanes). kClass only tells
-// length classes that share the other parameters apart (one symbol per class,
-// so that profiles attribute launches to classes).
-template <int NT, bool kSmemState, int G = 32, int kClass = 0>
+// ballots and barriers then name only the group's lanes). kCompact (shared
+// state only): keep (x_p, v_p) and the term count, and form w_p, q_p where
+// they are used; this holds 1.8x the nonzeros in the same shared memory for
+// one reciprocal more per list entry and evaluation.
+// kCluster (CTA groups with shared state): a unit is split over the CTAs of a
+// thread-block cluster. CTA c stages and owns the contiguous slice [c*Lc,
+// (c+1)*Lc) of the unit's nonzeros (Lc = ceil(L / cluster size)), with its
+// own lists and state. Every evaluation reduces inside the CTA, then warp 0
+// stores the CTA partial into slot [rank] of every CTA of the cluster through
+// distributed shared memory and arrives on that CTA's mbarrier; each thread
+// waits on its own CTA's mbarrier (bounded by a clock limit: on timeout the
+// error flag is set and later exchanges are skipped) and sums the slots in
+// rank order, so that all threads of all CTAs hold identical totals and take
+// identical Newton decisions. (One store and arrival per warp instead, with
+// no CTA barrier, was slower: 128 arrivals per mbarrier and evaluation at 8
+// CTAs.) Clusters take units from the bucket's queue, longest first.
+template <int NT, bool kSmemState, int G = 32, bool kCompact = false, bool kCluster = false>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kSmemState>())) sparse_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
     static_assert(G == 32 || !kCta, "sub-warp groups are warp-level");
+    static_assert(!kCluster || (kCta && kSmemState), "clusters split CTA groups with shared state");
     constexpr int kNW = NT / 32;
     constexpr int E = kCta ? kSparseECta : kSparseE;
     constexpr int CH = kCta ? 32 : G;   // lanes per chunk of nonzeros (a warp, or the group)
@@ -1074,7 +1099,8 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
 
     const int r = a.r, ldr = a.ldr, lcap = a.lcap, nf4 = ldr >> 2;
     const int LW = lcap / kNW;
-    const SparseLayout lay = sparse_layout(r, ldr, NT, kSmemState ? lcap : 0);
+    const SparseLayout lay = sparse_layout(r, ldr, NT, kSmemState ? lcap : 0, kCompact);
+    constexpr bool kWQ = !(kSmemState && kCompact);  // w_p, q_p stored
     unsigned char *gs = smem_raw + (size_t)group_in_block * lay.bytes;
     uint8_t *perm = gs;
     float *x_init = reinterpret_cast<float *>(gs + 256);
@@ -1084,11 +1110,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
     float2 *red = reinterpret_cast<float2 *>(gs + lay.red_off);
     float *slot = a.scratch + (int64_t)group_global * a.slot_floats;
     int2 *mylists = reinterpret_cast<int2 *>(slot) + (int64_t)w * r * LW;
-    float2 *xv, *wq;
+    float2 *xv, *wq = nullptr;
     uint16_t *tm;
     if constexpr (kSmemState) {
+        // compact: w_p = v_p/(x_p+eps) and q_p = w_p/(x_p+eps) are formed
+        // where they are used, with the same operations as where they are stored
         xv = reinterpret_cast<float2 *>(gs + lay.xv_off);
-        wq = reinterpret_cast<float2 *>(gs + lay.wq_off);
+        if constexpr (!kCompact) wq = reinterpret_cast<float2 *>(gs + lay.wq_off);
         tm = reinterpret_cast<uint16_t *>(gs + lay.tm_off);
     } else {
         // interleaved (x_p, v_p, w_p, q_p) per nonzero: one 16-byte piece, so a
@@ -1105,9 +1133,52 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
     int parity = 0;
     if (tid_g == 0) {  // the dummy entry's state: zero, and it stays zero
         xv[XS * (lcap)] = make_float2(0.f, 0.f);
-        wq[XS * (lcap)] = make_float2(0.f, 0.f);
+        if constexpr (kWQ) wq[XS * (lcap)] = make_float2(0.f, 0.f);
         tm[lcap] = 0;
     }
+
+    // cluster exchange: slots [2][kClusterMax] and two mbarriers after the layout
+    uint32_t crank = 0, csize = 1;
+    unsigned long long *xslots = reinterpret_cast<unsigned long long *>(smem_raw + lay.bytes);
+    unsigned long long *xbar = xslots + 2 * kClusterMax;
+    __shared__ int s_abort;
+    uint32_t xphase[2] = {0u, 0u};
+    int xpar = 0;
+    if constexpr (kCluster) {
+        cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+        crank = cluster.block_rank();
+        csize = cluster.num_blocks();
+        if (threadIdx.x == 0) {
+            mbar_init(smem_addr(&xbar[0]), csize);
+            mbar_init(smem_addr(&xbar[1]), csize);
+            s_abort = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        cluster.sync();
+    }
+    // Sum over the cluster of one 64-bit value per CTA (`mine`, meaningful in
+    // warp 0); `combine` reads the csize slots in rank order.
+    auto cluster_sum = [&](unsigned long long mine, auto &&combine) {
+        const uint32_t bar = smem_addr(&xbar[xpar]);
+        if (!*reinterpret_cast<volatile int *>(&s_abort)) {
+            if (warp_in_block == 0 && lane < (int)csize) {
+                const uint32_t slot = smem_addr(&xslots[xpar * kClusterMax + crank]);
+                st_cluster_u64(map_rank(slot, lane), mine);
+                mbar_arrive_remote(map_rank(bar, lane));
+            }
+            const long long t0 = clock64();
+            while (!mbar_try_wait(bar, xphase[xpar])) {
+                if (clock64() - t0 > kWaitCycles) {
+                    s_abort = 1;
+                    atomicOr(a.err, 2);
+                    break;
+                }
+            }
+        }
+        combine(xslots + xpar * kClusterMax, (int)csize);
+        xphase[xpar] ^= 1u;
+        xpar ^= 1;
+    };
 
     auto group_sync = [&]() {
         if constexpr (kCta) __syncthreads(); else __syncwarp(gmask);
@@ -1118,7 +1189,30 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             sg += __shfl_xor_sync(gmask, sg, o);
             sh += __shfl_xor_sync(gmask, sh, o);
         }
-        if constexpr (kCta) {
+        if constexpr (kCluster) {
+            float2 *rb = red + parity * kNW;
+            if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
+            __syncthreads();
+            parity ^= 1;
+            float cg = 0.f, ch = 0.f;
+            if (warp_in_block == 0) {
+#pragma unroll
+                for (int i = 0; i < kNW; ++i) {
+                    const float2 v = rb[i];
+                    cg += v.x;
+                    ch += v.y;
+                }
+            }
+            float2 tot = make_float2(0.f, 0.f);
+            cluster_sum(pack_f2(cg, ch), [&](const unsigned long long *sl, int n) {
+                for (int i = 0; i < n; ++i) {
+                    const float2 v = unpack_f2(sl[i]);
+                    tot.x += v.x;
+                    tot.y += v.y;
+                }
+            });
+            return tot;
+        } else if constexpr (kCta) {
             float2 *rb = red + parity * kNW;
             if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
             __syncthreads();
@@ -1138,7 +1232,20 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
 
     for (;;) {
         int qi;
-        if constexpr (kCta) {
+        if constexpr (kCluster) {
+            // rank 0 takes the next unit and hands it to every CTA of the
+            // cluster (the first barrier: every CTA has read the last one)
+            cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+            cluster.sync();
+            if (crank == 0 && threadIdx.x < csize) {
+                int q = 0;
+                if (threadIdx.x == 0) q = atomicAdd(a.queue, 1);
+                q = __shfl_sync((1u << csize) - 1u, q, 0);
+                st_cluster_u32(map_rank(smem_addr(&s_q), threadIdx.x), (uint32_t)q);
+            }
+            cluster.sync();
+            qi = s_q;
+        } else if constexpr (kCta) {
             __syncthreads();
             if (threadIdx.x == 0) s_q = atomicAdd(a.queue, 1);
             __syncthreads();
@@ -1151,10 +1258,17 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
         }
         if (qi >= count) break;
         const int64_t u = a.units[qi];
-        const int64_t base = a.ptr[u];
-        const int L = (int)(a.ptr[u + 1] - base);
+        int64_t base = a.ptr[u];
+        int L = (int)(a.ptr[u + 1] - base);
         const int64_t perm_unit = a.unit_ids ? a.unit_ids[u] : u;
-        if (L > lcap) {  // cannot happen with a consistent plan; refuse rather than overrun
+        // clusters: this CTA's slice (the same Lc, hence the same test, on every rank)
+        const int Lc = (L + (int)csize - 1) / (int)csize;
+        if constexpr (kCluster) {
+            const int my0 = min(L, (int)crank * Lc);
+            base += my0;
+            L = min(Lc, L - my0);
+        }
+        if (Lc > lcap) {  // cannot happen with a consistent plan; refuse rather than overrun
             if (tid_g == 0) atomicOr(a.err, 4);
             continue;
         }
@@ -1220,9 +1334,11 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             }
             if (valid) {
                 const float xl = terms == 0 ? 0.f : acc;
-                const float ri = recip(xl + eps_div);
                 xv[XS * (p)] = make_float2(xl, v);
-                wq[XS * (p)] = make_float2(v * ri, v * ri * ri);
+                if constexpr (kWQ) {
+                    const float ri = recip(xl + eps_div);
+                    wq[XS * (p)] = make_float2(v * ri, v * ri * ri);
+                }
                 tm[p] = (uint16_t)terms;
             }
             __syncwarp(gmask);
@@ -1273,9 +1389,17 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                 auto eval = [&]() -> float2 {
                     float sg = 0.f, sh = 0.f;
                     auto acc = [&](int p, float av) {
-                        const float2 st = wq[XS * (p)];
-                        sg = fmaf(st.x, av, sg);
-                        sh = fmaf(st.y * av, av, sh);
+                        if constexpr (kCompact) {
+                            const float2 st = xv[p];
+                            const float ri = recip(st.x + eps_div);
+                            const float wp = st.y * ri, qp = wp * ri;
+                            sg = fmaf(wp, av, sg);
+                            sh = fmaf(qp * av, av, sh);
+                        } else {
+                            const float2 st = wq[p];
+                            sg = fmaf(st.x, av, sg);
+                            sh = fmaf(st.y * av, av, sh);
+                        }
                     };
 #pragma unroll
                     for (int t = 0; t < E; ++t)
@@ -1285,13 +1409,21 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                 };
                 auto update = [&](float d, int dc) {
                     auto upd = [&](int p, float av) {
-                        const float2 st = xv[XS * (p)];
-                        int terms = dc != 0 ? (int)tm[p] : 0;
-                        const float xn = step_x(st.x, av, d, dc, terms);
-                        if (dc != 0) tm[p] = (uint16_t)terms;
-                        const float ri = recip(xn + eps_div);
-                        xv[XS * (p)].x = xn;
-                        wq[XS * (p)] = make_float2(st.y * ri, st.y * ri * ri);
+                        if constexpr (kCompact) {
+                            const float x0 = xv[p].x;
+                            int terms = dc != 0 ? (int)tm[p] : 0;
+                            const float xn = step_x(x0, av, d, dc, terms);
+                            if (dc != 0) tm[p] = (uint16_t)terms;
+                            xv[p].x = xn;
+                        } else {
+                            const float2 st = xv[p];
+                            int terms = dc != 0 ? (int)tm[p] : 0;
+                            const float xn = step_x(st.x, av, d, dc, terms);
+                            if (dc != 0) tm[p] = (uint16_t)terms;
+                            const float ri = recip(xn + eps_div);
+                            xv[p].x = xn;
+                            wq[p] = make_float2(st.y * ri, st.y * ri * ri);
+                        }
                     };
 #pragma unroll
                     for (int t = 0; t < E; ++t)
@@ -1413,7 +1545,21 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             double dt = (double)t;
 #pragma unroll
             for (int o = CH / 2; o > 0; o >>= 1) dt += __shfl_xor_sync(gmask, dt, o);
-            if constexpr (kCta) {
+            if constexpr (kCluster) {
+                double *rd = reinterpret_cast<double *>(red + parity * kNW);
+                if (lane == 0) rd[warp_in_block] = dt;
+                __syncthreads();
+                parity ^= 1;
+                double cta = 0.0;
+                if (warp_in_block == 0)
+                    for (int i = 0; i < kNW; ++i) cta += rd[i];
+                cluster_sum(static_cast<unsigned long long>(__double_as_longlong(cta)),
+                            [&](const unsigned long long *sl, int n) {
+                                double tot = 0.0;
+                                for (int i = 0; i < n; ++i) tot += __longlong_as_double(static_cast<long long>(sl[i]));
+                                dt = tot;
+                            });
+            } else if constexpr (kCta) {
                 double *rd = reinterpret_cast<double *>(red + parity * kNW);
                 if (lane == 0) rd[warp_in_block] = dt;
                 __syncthreads();
@@ -1423,7 +1569,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                 parity ^= 1;
                 dt = tot;
             }
-            if (tid_g == 0) a.unit_obj[u] = dt;
+            if (tid_g == 0 && crank == 0) a.unit_obj[u] = dt;
         }
         group_sync();
         // drop this warp's finished list lines from L2 (whole lines only)
@@ -1432,13 +1578,17 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             const char *l0 = reinterpret_cast<const char *>(mylists + (int64_t)k * LW);
             for (int i = glane; i < lines; i += CH) asm volatile("discard.global.L2 [%0], 128;" ::"l"(l0 + 128 * i) : "memory");
         }
-        for (int k = tid_g; k < r; k += GS) {
-            const float xk = x_out[k];
-            if (!(xk == xk)) atomicOr(a.err, 1);
-            a.X[u * ldr + k] = xk;
+        if (crank == 0) {
+            for (int k = tid_g; k < r; k += GS) {
+                const float xk = x_out[k];
+                if (!(xk == xk)) atomicOr(a.err, 1);
+                a.X[u * ldr + k] = xk;
+            }
         }
     }
-    if (tid_g == 0) flush_tally(a, tally);
+    if (tid_g == 0 && crank == 0) flush_tally(a, tally);
+    // no CTA of a cluster may leave while a peer can still write into its shared memory
+    if constexpr (kCluster) cooperative_groups::this_cluster().sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -1511,44 +1661,84 @@ struct SparseKind {
     int g;           // lanes per warp-level group (8, 16 or 32)
     int cap;         // longest unit (nonzeros) of the class; 0: no limit
     bool smem;       // per-nonzero state in shared memory (else in the slot)
+    bool compact;    // shared state without w_p, q_p
+    int cl;          // CTAs per cluster (1: no cluster)
     int max_groups;  // resident groups per SM at most (0: as many as fit)
     const char *name;
 };
 // Short units on 8 or 16 lanes (four or two units per warp), one warp per
 // unit up to 1,024 nonzeros, then one CTA of 128 / 256 / 512 threads per unit
-// up to 2,048 / 4,096 nonzeros / as many as its shared memory holds (about
-// 12,000 at r = 100), all with the per-nonzero state in shared memory; past
-// that one 512-thread CTA per unit with the state in the slot. A class whose
-// shared-memory layout does not fit passes its units on to the next one (at
-// r <= 256 the 128- and 256-thread layouts always fit, the 512-thread one up
-// to at least 11,264 nonzeros). One warp per unit with the state in the slot,
-// for 1,025..8,192 nonzeros, measured 9% slower per step at r = 100.
+// up to 2,048 / 4,096 nonzeros / as many as its shared memory holds (22,016
+// at r = 100), then a cluster of 2, 4, 8 or 16 such 512-thread CTAs (the
+// smallest whose slices fit), all with the per-nonzero state in shared
+// memory; past that (or where no cluster can be scheduled) one 512-thread CTA
+// per unit with the state in the slot. A class whose shared-memory layout does
+// not fit passes its units on to the next one (at r <= 256 the 128- and
+// 256-thread layouts always fit, the 512-thread one up to at least 20,992
+// nonzeros). One warp per unit with the state in the slot, for 1,025..8,192
+// nonzeros, measured 9% slower per step at r = 100.
+#define NMFKL_SPARSE_CLU sparse_kernel<512, true, 32, true, true>
 const SparseKind kSparseKinds[] = {
-    {(const void *)sparse_kernel<32, true, 8>, 32, 8, 64, true, 0, "sparse_g8"},
-    {(const void *)sparse_kernel<32, true, 16>, 32, 16, 128, true, 0, "sparse_g16"},
-    {(const void *)sparse_kernel<32, true>, 32, 32, 512, true, 0, "sparse_warp"},
-    {(const void *)sparse_kernel<32, true, 32, 1>, 32, 32, 1024, true, 0, "sparse_warp_1k"},
-    {(const void *)sparse_kernel<128, true>, 128, 32, 2048, true, 0, "sparse_cta128"},
-    {(const void *)sparse_kernel<256, true>, 256, 32, 4096, true, 0, "sparse_cta256"},
-    {(const void *)sparse_kernel<512, true>, 512, 32, 16384, true, 0, "sparse_cta512"},
-    {(const void *)sparse_kernel<512, false>, 512, 32, 0, false, 0, "sparse_giant"},
+    {(const void *)sparse_kernel<32, true, 8>, 32, 8, 64, true, false, 1, 0, "sparse_g8"},
+    {(const void *)sparse_kernel<32, true, 16>, 32, 16, 128, true, false, 1, 0, "sparse_g16"},
+    {(const void *)sparse_kernel<32, true>, 32, 32, 512, true, false, 1, 0, "sparse_warp"},
+    {(const void *)sparse_kernel<32, true, 32, true>, 32, 32, 1024, true, true, 1, 0, "sparse_warp_1k"},
+    {(const void *)sparse_kernel<128, true>, 128, 32, 2048, true, false, 1, 0, "sparse_cta128"},
+    {(const void *)sparse_kernel<256, true>, 256, 32, 4096, true, false, 1, 0, "sparse_cta256"},
+    {(const void *)sparse_kernel<512, true, 32, true>, 512, 32, 1 << 30, true, true, 1, 0, "sparse_cta512"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 1 << 30, true, true, 2, 0, "sparse_cluster2"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 1 << 30, true, true, 4, 0, "sparse_cluster4"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 1 << 30, true, true, 8, 0, "sparse_cluster8"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 1 << 30, true, true, 16, 0, "sparse_cluster16"},
+    {(const void *)sparse_kernel<512, false>, 512, 32, 0, false, false, 1, 0, "sparse_giant"},
 };
+#undef NMFKL_SPARSE_CLU
 constexpr int kNumSparseKinds = sizeof(kSparseKinds) / sizeof(kSparseKinds[0]);
 
-// Row length of a unit of L nonzeros in a group of the kind (whole chunks of
-// every warp of the group).
+// Row length of a unit of L nonzeros in a group of the kind: its slice (a
+// cluster's CTAs split the unit) in whole chunks of every warp of the group.
 int64_t sparse_lcap(const SparseKind &sk, int64_t L) {
     const int64_t chunk = sk.nt > 32 ? sk.nt : sk.g;
-    return std::max<int64_t>(chunk, (L + chunk - 1) / chunk * chunk);
+    const int64_t slice = (L + sk.cl - 1) / sk.cl;
+    return std::max<int64_t>(chunk, (slice + chunk - 1) / chunk * chunk);
 }
 
-// The first class whose cap holds L and, for shared-memory state, whose
-// group layout fits the per-block limit.
-int sparse_kind_for_length(int64_t L, int r, int ldr, int optin) {
+// Dynamic shared memory of one group of the kind at row length lcap: the
+// layout, plus for clusters the exchange slots and mbarriers.
+size_t sparse_group_smem(const SparseKind &sk, int r, int ldr, int64_t lcap) {
+    size_t b = sparse_layout(r, ldr, sk.nt, sk.smem ? (int)lcap : 0, sk.compact).bytes;
+    if (sk.cl > 1) b += (2 * (size_t)kClusterMax + 2) * sizeof(unsigned long long);
+    return b;
+}
+
+// Clusters of the kind that can be resident at once at the given shared memory.
+int sparse_active_clusters(const SparseKind &sk, size_t smem) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(sk.cl);
+    cfg.blockDim = dim3(sk.nt);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = sk.cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, sk.fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+// The first usable class whose cap holds L and, for shared-memory state,
+// whose group layout fits the per-block limit.
+int sparse_kind_for_length(int64_t L, int r, int ldr, int optin, const std::vector<char> &usable) {
     for (int i = 0; i < kNumSparseKinds - 1; ++i) {
         const SparseKind &sk = kSparseKinds[i];
-        if (L > sk.cap) continue;
-        if (sk.smem && sparse_layout(r, ldr, sk.nt, (int)sparse_lcap(sk, L)).bytes > (size_t)optin) continue;
+        if (!usable[i] || L > sk.cap) continue;
+        if (sk.smem && sparse_group_smem(sk, r, ldr, sparse_lcap(sk, L)) > (size_t)optin) continue;
         return i;
     }
     return kNumSparseKinds - 1;
@@ -1580,9 +1770,17 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
     const int r = c->p.r, ldr = c->ldr;
     std::vector<std::vector<int32_t>> lists(kNumSparseKinds);
     std::vector<int64_t> maxlen(kNumSparseKinds, 0), nnz(kNumSparseKinds, 0);
+    // cluster classes that the device can schedule (at the largest shared memory they may take)
+    std::vector<char> usable(kNumSparseKinds, 1);
+    std::vector<int> clusters_fit(kNumSparseKinds, 0);
+    for (int i = 0; i < kNumSparseKinds; ++i) {
+        if (kSparseKinds[i].cl <= 1) continue;
+        clusters_fit[i] = sparse_active_clusters(kSparseKinds[i], (size_t)optin);
+        usable[i] = clusters_fit[i] > 0;
+    }
     for (int64_t u = 0; u < units; ++u) {
         const int64_t L = ptr[u + 1] - ptr[u];
-        const int kind = sparse_kind_for_length(L, r, ldr, optin);
+        const int kind = sparse_kind_for_length(L, r, ldr, optin, usable);
         lists[kind].push_back((int32_t)u);
         maxlen[kind] = std::max(maxlen[kind], L);
         nnz[kind] += L;
@@ -1601,12 +1799,12 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
         b.kind = kind;
         b.nt = sk.nt;
         b.k = 0;
-        b.cl = 1;
+        b.cl = sk.cl;
         b.count = (int32_t)lst.size();
         b.max_len = maxlen[kind];
         b.nnz = nnz[kind];
         b.lcap = (int32_t)sparse_lcap(sk, b.max_len);
-        const size_t gbytes = sparse_layout(r, ldr, sk.nt, smem_state ? b.lcap : 0).bytes;
+        const size_t gbytes = sparse_group_smem(sk, r, ldr, b.lcap);
         int gpb = 1;
         if (!cta) {
             // warps per block: the most resident warps per SM that shared memory allows
@@ -1638,6 +1836,14 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
         if (sk.max_groups > 0) per_sm = std::max(1, std::min(per_sm, sk.max_groups / gpb));
         const int64_t need_blocks = (b.count + gpb - 1) / gpb;
         b.grid = (int)std::min<int64_t>(need_blocks, (int64_t)per_sm * c->num_sms);
+        if (sk.cl > 1) {  // whole clusters, as many as can be resident (one unit each at a time)
+            const int nclu = sparse_active_clusters(sk, b.smem);
+            if (nclu < 1) {
+                c->err = std::string("kernel ") + sk.name + " cannot be resident";
+                return NMFKL_EINVAL;
+            }
+            b.grid = (int)std::min<int64_t>(b.count, nclu) * sk.cl;
+        }
         b.groups = b.grid * gpb;
         b.slot_floats = sparse_slot_floats(r, b.lcap, smem_state);
         if (!cuda_ok(c, cudaMalloc(&b.d_units, sizeof(int32_t) * lst.size()), "alloc unit list")) return NMFKL_ENOMEM;
@@ -1823,7 +2029,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
         void *args[] = {&a};
         const int tok = timer_begin(c, bucket_name(b));
         cudaError_t e;
-        if (b.sparse) {
+        if (b.sparse && b.cl == 1) {
             e = cudaLaunchKernel(kSparseKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
         } else if (b.cl > 1) {
             cudaLaunchConfig_t cfg{};
@@ -1838,7 +2044,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            e = cudaLaunchKernelExC(&cfg, kKinds[b.kind].fn, args);
+            e = cudaLaunchKernelExC(&cfg, b.sparse ? kSparseKinds[b.kind].fn : kKinds[b.kind].fn, args);
         } else {
             e = cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
         }
@@ -2301,6 +2507,9 @@ cudaError_t kernel_attributes(int device) {
         }
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kKinds[kGiantKind - 1].fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (int i = 0; e == cudaSuccess && i < kNumSparseKinds; ++i)
+            if (kSparseKinds[i].cl > 1)
+                e = cudaFuncSetAttribute(kSparseKinds[i].fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         g_attr_err[device] = e;
     });
     return g_attr_err[device];

@@ -32,7 +32,7 @@ LIST_MODES = [1, 2]
 
 BUCKET_LENGTHS = [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513,
                   1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 12000,
-                  12799, 12800, 12801, 13500]
+                  22527, 22528, 22529, 23041]
 
 
 @pytest.fixture(scope="module")
@@ -44,7 +44,7 @@ def torch():
 
 @pytest.fixture(scope="module")
 def designed():
-    return designed_matrix(14000, 14000, BUCKET_LENGTHS, BUCKET_LENGTHS, seed=1)
+    return designed_matrix(23500, 23500, BUCKET_LENGTHS, BUCKET_LENGTHS, seed=1)
 
 
 @pytest.fixture(scope="module")
@@ -158,7 +158,7 @@ def test_designed_lengths_reach_every_list_class(designed):
     W0, F0 = start(designed, r, seed=2)
     m = model(designed, W0, F0, params(r, seed=5, list_mode=2))
     want = {"sparse_g8", "sparse_g16", "sparse_warp", "sparse_warp_1k", "sparse_cta128", "sparse_cta256",
-            "sparse_cta512", "sparse_giant"}
+            "sparse_cta512", "sparse_cluster2"}
     for side in (0, 1):
         kinds = {b["kernel"] for b in m.plan() if b["side"] == side and b["kernel"].startswith("sparse_")}
         assert want <= kinds, (side, want - kinds)
@@ -167,9 +167,9 @@ def test_designed_lengths_reach_every_list_class(designed):
 
 @pytest.mark.parametrize("list_mode", LIST_MODES)
 def test_halves_tight_every_bucket(designed, list_mode):
-    """Unit lengths 0..13500 around every bucket edge (warp K=1..16, CTA,
-    clusters, giant; sparse-list sub-warp, warp, CTA and giant classes; at
-    r = 16 the 512-thread shared-state list class ends at 12,800)."""
+    """Unit lengths 0..23041 around every bucket edge (warp K=1..16, CTA,
+    clusters, giant; sparse-list sub-warp, warp, CTA and cluster classes; at
+    r = 16 the 512-thread shared-state list class ends at 22,528)."""
     V = designed
     r = 16
     W0, F0 = start(V, r, seed=2)
@@ -375,7 +375,8 @@ def test_invalid_arguments(torch):
 @pytest.mark.parametrize("list_mode", LIST_MODES)
 def test_long_rows_every_cluster_size(list_mode):
     """Rows of 9k..99k nonzeros: CTA, cluster-of-2/4/8/16 and (beyond) giant
-    kernels on the W half, against the oracle from an identical state."""
+    dense kernels, or the CTA and cluster-of-2/4/8 list kernels, on the W
+    half, against the oracle from an identical state."""
     rng = np.random.default_rng(4)
     n, m = 64, 100_000
     lens = [9_000, 13_000, 20_000, 30_000, 45_000, 60_000, 80_000, 99_000]
@@ -397,10 +398,42 @@ def test_long_rows_every_cluster_size(list_mode):
     m_ = model(V, W0, F0, p)
     kinds = {b["kernel"] for b in m_.plan() if b["side"] == 1}
     assert any(k.startswith("sweep_cluster") for k in kinds), kinds
-    assert "sparse_giant" in kinds and "sparse_cta512" in kinds, kinds
+    assert {"sparse_cta512", "sparse_cluster2", "sparse_cluster4", "sparse_cluster8"} <= kinds, kinds
     m_.sweep_W(0)
     Wg = m_.get_W()
     m_.close()
     Wo, _ = oracle.half_W(V, W0, F0, 8, 0, cfg_for(p, 1), threads=8)
+    dev, _ = fp32_sensitivity(V, W0, F0, 1, p, Wo)
+    assert within(Wg, Wo, slack=PROBE_FACTOR * dev).all()
+
+
+def test_list_rows_beyond_clusters():
+    """Rows of 30k..400k nonzeros on the list path: clusters of 2/4/8/16 CTAs
+    (where the device schedules 16) and, past sixteen slices of shared
+    state, the slot-state giant kernel; W half against the oracle."""
+    rng = np.random.default_rng(6)
+    n, m = 12, 420_000
+    lens = [400_000, 300_000, 150_000, 70_000, 30_000]
+    rows, cols = [], []
+    for i, L in enumerate(lens):
+        rows.append(np.full(L, i)); cols.append(np.sort(rng.choice(m, size=L, replace=False)))
+    extra = rng.integers(0, m, size=m)
+    rows.append(rng.integers(len(lens), n, size=extra.size)); cols.append(extra)
+    R = np.concatenate(rows); C = np.concatenate(cols)
+    key = np.unique(C.astype(np.int64) * n + R)
+    C, R = key // n, key % n
+    colptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(C, minlength=m), out=colptr[1:])
+    V = synth.from_csc(n, m, colptr, R.astype(np.int32), rng.integers(1, 6, size=R.size).astype(np.float32))
+    r = 12
+    W0, F0 = start(V, r, seed=4)
+    p = params(r, seed=9, list_mode=2, **TIGHT)
+    m_ = model(V, W0, F0, p)
+    kinds = {b["kernel"] for b in m_.plan() if b["side"] == 1}
+    assert {"sparse_giant", "sparse_cluster2", "sparse_cluster4", "sparse_cluster8"} <= kinds, kinds
+    m_.sweep_W(0)
+    Wg = m_.get_W()
+    m_.close()
+    Wo, _ = oracle.half_W(V, W0, F0, 9, 0, cfg_for(p, 1), threads=8)
     dev, _ = fp32_sensitivity(V, W0, F0, 1, p, Wo)
     assert within(Wg, Wo, slack=PROBE_FACTOR * dev).all()
