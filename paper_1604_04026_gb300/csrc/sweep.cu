@@ -1677,6 +1677,14 @@ struct SparseKind {
 // 256-thread layouts always fit, the 512-thread one up to at least 20,992
 // nonzeros). One warp per unit with the state in the slot, for 1,025..8,192
 // nonzeros, measured 9% slower per step at r = 100.
+// Nonzeros per 512-thread CTA (alone or in a cluster): at most 16,384, so that
+// at a density of up to 1/4 a warp's list of a coordinate (<= 256 entries)
+// fits the registers it prefetches into (longer lists read their tail from
+// global memory in the dependent chain of every evaluation and update).
+// Measured on the large corpus at r = 100: 117.6 ms per step at 16,384 vs
+// 121.3 at 12,288 (more units in clusters, which leave SMs idle) and 120.4
+// without a cap (22,016 by shared memory).
+constexpr int kSliceCap = 16384;
 #define NMFKL_SPARSE_CLU sparse_kernel<512, true, 32, true, true>
 const SparseKind kSparseKinds[] = {
     {(const void *)sparse_kernel<32, true, 8>, 32, 8, 64, true, false, 1, 0, "sparse_g8"},
@@ -1685,11 +1693,13 @@ const SparseKind kSparseKinds[] = {
     {(const void *)sparse_kernel<32, true, 32, true>, 32, 32, 1024, true, true, 1, 0, "sparse_warp_1k"},
     {(const void *)sparse_kernel<128, true>, 128, 32, 2048, true, false, 1, 0, "sparse_cta128"},
     {(const void *)sparse_kernel<256, true>, 256, 32, 4096, true, false, 1, 0, "sparse_cta256"},
-    {(const void *)sparse_kernel<512, true, 32, true>, 512, 32, 1 << 30, true, true, 1, 0, "sparse_cta512"},
-    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 1 << 30, true, true, 2, 0, "sparse_cluster2"},
-    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 1 << 30, true, true, 4, 0, "sparse_cluster4"},
-    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 1 << 30, true, true, 8, 0, "sparse_cluster8"},
-    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 1 << 30, true, true, 16, 0, "sparse_cluster16"},
+    {(const void *)sparse_kernel<512, true, 32, true>, 512, 32, kSliceCap, true, true, 1, 0, "sparse_cta512"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 2 * kSliceCap, true, true, 2, 0, "sparse_cluster2"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 3 * kSliceCap, true, true, 3, 0, "sparse_cluster3"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 4 * kSliceCap, true, true, 4, 0, "sparse_cluster4"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 6 * kSliceCap, true, true, 6, 0, "sparse_cluster6"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 8 * kSliceCap, true, true, 8, 0, "sparse_cluster8"},
+    {(const void *)NMFKL_SPARSE_CLU, 512, 32, 16 * kSliceCap, true, true, 16, 0, "sparse_cluster16"},
     {(const void *)sparse_kernel<512, false>, 512, 32, 0, false, false, 1, 0, "sparse_giant"},
 };
 #undef NMFKL_SPARSE_CLU

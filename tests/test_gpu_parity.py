@@ -408,12 +408,12 @@ def test_long_rows_every_cluster_size(list_mode):
 
 
 def test_list_rows_beyond_clusters():
-    """Rows of 30k..400k nonzeros on the list path: clusters of 2/4/8/16 CTAs
-    (where the device schedules 16) and, past sixteen slices of shared
-    state, the slot-state giant kernel; W half against the oracle."""
+    """Rows of 20k..400k nonzeros on the list path: clusters of 2/3/4/6/8/16
+    CTAs (16 where the device schedules it) and, past sixteen slices, the
+    slot-state giant kernel; W half against the oracle."""
     rng = np.random.default_rng(6)
     n, m = 12, 420_000
-    lens = [400_000, 300_000, 150_000, 70_000, 30_000]
+    lens = [400_000, 300_000, 150_000, 110_000, 90_000, 60_000, 40_000, 20_000]
     rows, cols = [], []
     for i, L in enumerate(lens):
         rows.append(np.full(L, i)); cols.append(np.sort(rng.choice(m, size=L, replace=False)))
@@ -430,7 +430,8 @@ def test_list_rows_beyond_clusters():
     p = params(r, seed=9, list_mode=2, **TIGHT)
     m_ = model(V, W0, F0, p)
     kinds = {b["kernel"] for b in m_.plan() if b["side"] == 1}
-    assert {"sparse_giant", "sparse_cluster2", "sparse_cluster4", "sparse_cluster8"} <= kinds, kinds
+    assert {"sparse_giant", "sparse_cluster2", "sparse_cluster3", "sparse_cluster4", "sparse_cluster6",
+            "sparse_cluster8"} <= kinds, kinds
     m_.sweep_W(0)
     Wg = m_.get_W()
     m_.close()
