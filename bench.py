@@ -163,9 +163,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload, r):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the summary is absent or the kernel source changed since."""
+def ncu_traffic(kernel, half, workload, r):
+    """DRAM bytes per launch of `kernel` on `half` ("F" or "W") from the
+    committed ncu summary, or None when the summary is absent or the kernel
+    source changed since."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
@@ -174,7 +175,7 @@ def ncu_traffic(kernel, workload, r):
         return None
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    entry = d.get("kernels", {}).get("%s/%s/r%d" % (workload, kernel, r))
+    entry = d.get("kernels", {}).get("%s/%s/%s/r%d" % (workload, kernel, half, r))
     return None if entry is None else entry.get("dram_bytes_per_launch_full")
 
 
@@ -306,28 +307,25 @@ def run_ours(args):
     plan_all = model.plan()  # both plans (dense tile, sparse lists) of both halves
     value = ws * U * args.steps / (ms / 1e3)
 
-    # roofline of the dominant kernel family: its algorithmic bytes per launch
-    # (the mean over the buckets of that kernel, one per half it serves) over
-    # its mean launch time in the timed steps
+    # roofline of the dominant kernel (timers are per kernel and half,
+    # "<kernel>/F" or "<kernel>/W"): the algorithmic bytes of its bucket (one
+    # per half; a dense bucket the list plan keeps is the same units) over its
+    # mean launch time in the timed steps
     peak, peak_kind = measured_peak_hbm()
-    fam = {}
-    for b in plan_all:
-        units = b["count"]
-        e = fam.setdefault(b["kernel"], {"bytes": 0, "nnz": 0, "units": 0})
-        e["bytes"] += algorithmic_bytes(b["nnz"], units, r)
-        e["nnz"] += b["nnz"]
-        e["units"] += units
     sweep_kernels = {k: v for k, v in times.items() if k.startswith(("sweep_", "sparse_"))}
     dom = max(sweep_kernels, key=lambda k: sweep_kernels[k][1])
     launches, dom_ms = sweep_kernels[dom]
     per_launch_ms = dom_ms / max(launches, 1)
-    nbuckets = sum(1 for b in plan_all if b["kernel"] == dom)
-    bytes_per_launch = fam[dom]["bytes"] / max(1, nbuckets)
+    dom_kernel, dom_half = dom.rsplit("/", 1)
+    dom_side = 0 if dom_half == "F" else 1
+    dom_bucket = next(b for b in plan_all if b["kernel"] == dom_kernel and b["side"] == dom_side)
+    bytes_per_launch = algorithmic_bytes(dom_bucket["nnz"], dom_bucket["count"], r)
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
-    # a step moves each half's bytes once, whichever plan runs it
-    step_bytes = sum(algorithmic_bytes(b["nnz"], b["count"], r) for b in plan_all if b["kernel"].startswith("sweep_"))
+    # a step moves each half's bytes once, whichever plan runs it (the dense
+    # plan has every unit of its half)
+    step_bytes = sum(algorithmic_bytes(b["nnz"], b["count"], r) for b in plan_all if not b["list_plan"])
     ms_step = ms / args.steps
-    traffic = ncu_traffic(dom, args.workload, r)
+    traffic = ncu_traffic(dom_kernel, dom_half, args.workload, r)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)",

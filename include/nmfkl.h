@@ -215,7 +215,8 @@ int32_t nmfkl_kernel_times(nmfkl_ctx *ctx, const char **names, int64_t *launches
                            int32_t cap, int32_t reset);
 
 /* Launch plans of the sweep kernels: one entry per length bucket, half and
- * path (each half has a dense-tile plan and a sparse-list plan). */
+ * plan (each half has a dense-tile plan and a sparse-list plan; the list plan
+ * keeps the dense-tile buckets of its shortest units). */
 typedef struct {
     const char *kernel;  /* kernel family name (static storage) */
     int32_t side;        /* 0 = F half (columns), 1 = W half (rows) */
@@ -226,6 +227,7 @@ typedef struct {
     int64_t smem;        /* dynamic shared memory per block, bytes */
     int32_t ran_last;    /* 1 if the last half of this side ran this bucket's plan
                             (dense tile or sparse lists, see list_mode) */
+    int32_t list_plan;   /* 1: the bucket belongs to the list plan, 0: to the dense plan */
 } nmfkl_bucket_info;
 
 /* Fills up to `cap` entries; returns the number of buckets (-1 on a NULL ctx). */

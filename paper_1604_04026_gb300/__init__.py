@@ -202,12 +202,13 @@ class NMFKL:
 
     def plan(self) -> list:
         """Launch plan: one dict per (half, length bucket)."""
-        cap = 64
+        cap = 128
         arr = (_native.BucketInfo * cap)()
         nb = self._lib.nmfkl_plan_info(self._h, arr, cap)
         return [{"kernel": arr[i].kernel.decode(), "side": arr[i].side, "count": arr[i].count,
                  "nnz": arr[i].nnz, "max_len": arr[i].max_len, "grid": arr[i].grid,
-                 "block": arr[i].block, "smem": arr[i].smem, "ran_last": bool(arr[i].ran_last)}
+                 "block": arr[i].block, "smem": arr[i].smem, "ran_last": bool(arr[i].ran_last),
+                 "list_plan": bool(arr[i].list_plan)}
                 for i in range(min(nb, cap))]
 
     def _get(self, fn, rows, cols, out):

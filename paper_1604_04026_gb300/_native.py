@@ -29,7 +29,8 @@ class Counters(ctypes.Structure):
 
 class BucketInfo(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_char_p), ("side", c_i32), ("count", c_i32), ("nnz", c_i64),
-                ("max_len", c_i64), ("grid", c_i32), ("block", c_i32), ("smem", c_i64), ("ran_last", c_i32)]
+                ("max_len", c_i64), ("grid", c_i32), ("block", c_i32), ("smem", c_i64), ("ran_last", c_i32),
+                ("list_plan", c_i32)]
 
 
 class ServerCfg(ctypes.Structure):

@@ -609,8 +609,8 @@ int32_t nmfkl_plan_info(const nmfkl_ctx *c, nmfkl_bucket_info *out, int32_t cap)
     if (!c) return -1;
     int32_t i = 0;
     for (int side = 0; side < 2; ++side)
-        for (const auto *pl : {&c->plan[side], &c->plan_sparse[side]})
-        for (const auto &b : *pl) {
+        for (int lp = 0; lp < 2; ++lp)
+        for (const auto &b : lp ? c->plan_sparse[side] : c->plan[side]) {
             if (out && i < cap) {
                 out[i].kernel = bucket_name(b);
                 out[i].side = side;
@@ -620,7 +620,8 @@ int32_t nmfkl_plan_info(const nmfkl_ctx *c, nmfkl_bucket_info *out, int32_t cap)
                 out[i].grid = b.grid;
                 out[i].block = b.block;
                 out[i].smem = (int64_t)b.smem;
-                out[i].ran_last = c->used_sparse[side] == (b.sparse ? 1 : 0) ? 1 : 0;
+                out[i].ran_last = c->used_sparse[side] == lp ? 1 : 0;
+                out[i].list_plan = lp;
             }
             ++i;
         }

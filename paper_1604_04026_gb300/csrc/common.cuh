@@ -108,6 +108,7 @@ struct Bucket {
     int64_t slot_floats;
     int64_t max_len;
     int64_t nnz;      // nonzeros of the bucket's units
+    bool borrowed = false;  // a dense bucket reused by the list plan (d_units owned by the dense plan)
 };
 
 // Device state of fold-in (nmfkl_foldin): input copies, per-length-class

@@ -1059,11 +1059,9 @@ template <int NT, bool kSmemState>
 __host__ __device__ constexpr int sparse_min_blocks() {
     return NT == 32 ? 2 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
 }
-// G < 32: sub-warp groups, 32/G units per warp, each on G lanes (shuffles,
-// ballots and barriers then name only the group's lanes). kCompact (shared
-// state only): keep (x_p, v_p) and the term count, and form w_p, q_p where
-// they are used; this holds 1.8x the nonzeros in the same shared memory for
-// one reciprocal more per list entry and evaluation.
+// kCompact (shared state only): keep (x_p, v_p) and the term count, and form
+// w_p, q_p where they are used; this holds 1.8x the nonzeros in the same
+// shared memory for one reciprocal more per list entry and evaluation.
 // kCluster (CTA groups with shared state): a unit is split over the CTAs of a
 // thread-block cluster. CTA c stages and owns the contiguous slice [c*Lc,
 // (c+1)*Lc) of the unit's nonzeros (Lc = ceil(L / cluster size)), with its
@@ -1076,11 +1074,13 @@ __host__ __device__ constexpr int sparse_min_blocks() {
 // identical Newton decisions. (One store and arrival per warp instead, with
 // no CTA barrier, was slower: 128 arrivals per mbarrier and evaluation at 8
 // CTAs.) Clusters take units from the bucket's queue, longest first.
-template <int NT, bool kSmemState, int G = 32, bool kCompact = false, bool kCluster = false>
+template <int NT, bool kSmemState, bool kCompact = false, bool kCluster = false>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kSmemState>())) sparse_kernel(HalfArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
-    static_assert(G == 32 || !kCta, "sub-warp groups are warp-level");
+    // lanes per warp-level group: the whole warp (groups of 8 or 16 lanes,
+    // several units per warp, lost to the dense tile for units that short)
+    constexpr int G = 32;
     static_assert(!kCluster || (kCta && kSmemState), "clusters split CTA groups with shared state");
     constexpr int kNW = NT / 32;
     constexpr int E = kCta ? kSparseECta : kSparseE;
@@ -1666,17 +1666,17 @@ struct SparseKind {
     int max_groups;  // resident groups per SM at most (0: as many as fit)
     const char *name;
 };
-// Short units on 8 or 16 lanes (four or two units per warp), one warp per
-// unit up to 1,024 nonzeros, then one CTA of 128 / 256 / 512 threads per unit
-// up to 2,048 / 4,096 nonzeros / as many as its shared memory holds (22,016
-// at r = 100), then a cluster of 2, 4, 8 or 16 such 512-thread CTAs (the
-// smallest whose slices fit), all with the per-nonzero state in shared
-// memory; past that (or where no cluster can be scheduled) one 512-thread CTA
-// per unit with the state in the slot. A class whose shared-memory layout does
-// not fit passes its units on to the next one (at r <= 256 the 128- and
-// 256-thread layouts always fit, the 512-thread one up to at least 20,992
-// nonzeros). One warp per unit with the state in the slot, for 1,025..8,192
-// nonzeros, measured 9% slower per step at r = 100.
+// List classes (units of more than kDenseBelow nonzeros): one warp per unit
+// up to 1,024 nonzeros, then one CTA of 128 / 256 / 512 threads per unit up
+// to 2,048 / 4,096 / kSliceCap nonzeros, then a cluster of 2, 3, 4, 6, 8 or
+// 16 such 512-thread CTAs (the smallest whose slices hold kSliceCap), all
+// with the per-nonzero state in shared memory; past that (or where no cluster
+// can be scheduled) one 512-thread CTA per unit with the state in the slot.
+// A class whose shared-memory layout does not fit passes its units on to the
+// next one (at r <= 256 the 128- and 256-thread layouts always fit, the
+// 512-thread one up to at least 20,992 nonzeros). One warp per unit with the
+// state in the slot, for 1,025..8,192 nonzeros, measured 9% slower per step
+// at r = 100.
 // Nonzeros per 512-thread CTA (alone or in a cluster): at most 16,384, so that
 // at a density of up to 1/4 a warp's list of a coordinate (<= 256 entries)
 // fits the registers it prefetches into (longer lists read their tail from
@@ -1685,15 +1685,13 @@ struct SparseKind {
 // 121.3 at 12,288 (more units in clusters, which leave SMs idle) and 120.4
 // without a cap (22,016 by shared memory).
 constexpr int kSliceCap = 16384;
-#define NMFKL_SPARSE_CLU sparse_kernel<512, true, 32, true, true>
+#define NMFKL_SPARSE_CLU sparse_kernel<512, true, true, true>
 const SparseKind kSparseKinds[] = {
-    {(const void *)sparse_kernel<32, true, 8>, 32, 8, 64, true, false, 1, 0, "sparse_g8"},
-    {(const void *)sparse_kernel<32, true, 16>, 32, 16, 128, true, false, 1, 0, "sparse_g16"},
     {(const void *)sparse_kernel<32, true>, 32, 32, 512, true, false, 1, 0, "sparse_warp"},
-    {(const void *)sparse_kernel<32, true, 32, true>, 32, 32, 1024, true, true, 1, 0, "sparse_warp_1k"},
+    {(const void *)sparse_kernel<32, true, true>, 32, 32, 1024, true, true, 1, 0, "sparse_warp_1k"},
     {(const void *)sparse_kernel<128, true>, 128, 32, 2048, true, false, 1, 0, "sparse_cta128"},
     {(const void *)sparse_kernel<256, true>, 256, 32, 4096, true, false, 1, 0, "sparse_cta256"},
-    {(const void *)sparse_kernel<512, true, 32, true>, 512, 32, kSliceCap, true, true, 1, 0, "sparse_cta512"},
+    {(const void *)sparse_kernel<512, true, true>, 512, 32, kSliceCap, true, true, 1, 0, "sparse_cta512"},
     {(const void *)NMFKL_SPARSE_CLU, 512, 32, 2 * kSliceCap, true, true, 2, 0, "sparse_cluster2"},
     {(const void *)NMFKL_SPARSE_CLU, 512, 32, 3 * kSliceCap, true, true, 3, 0, "sparse_cluster3"},
     {(const void *)NMFKL_SPARSE_CLU, 512, 32, 4 * kSliceCap, true, true, 4, 0, "sparse_cluster4"},
@@ -1759,13 +1757,27 @@ int sparse_kind_for_length(int64_t L, int r, int ldr, int optin, const std::vect
 const char *kind_name(int kind) { return kKinds[kind].name; }
 const char *bucket_name(const Bucket &b) { return b.sparse ? kSparseKinds[b.kind].name : kKinds[b.kind].name; }
 
+// Kernel timer name of a bucket: "<kernel>/F" or "<kernel>/W" (static storage).
+const char *bucket_timer_name(const Bucket &b, int side) {
+    static const std::vector<std::string> names = [] {
+        std::vector<std::string> v;
+        for (int s = 0; s < 2; ++s) {
+            for (int i = 0; i < kNumKinds; ++i) v.push_back(std::string(kKinds[i].name) + (s ? "/W" : "/F"));
+            for (int i = 0; i < kNumSparseKinds; ++i) v.push_back(std::string(kSparseKinds[i].name) + (s ? "/W" : "/F"));
+        }
+        return v;
+    }();
+    const int per = kNumKinds + kNumSparseKinds;
+    return names[side * per + (b.sparse ? kNumKinds + b.kind : b.kind)].c_str();
+}
+
 
 
 void free_plan(nmfkl_ctx *c) {
     for (int side = 0; side < 2; ++side) {
         for (auto *pl : {&c->plan[side], &c->plan_sparse[side]}) {
             for (auto &b : *pl)
-                if (b.d_units) cudaFree(b.d_units);
+                if (b.d_units && !b.borrowed) cudaFree(b.d_units);
             pl->clear();
         }
     }
@@ -1773,8 +1785,17 @@ void free_plan(nmfkl_ctx *c) {
 
 namespace {
 
-// Sparse-list plan of one half: one bucket per length class; a class's tile
-// row length is its longest unit rounded up to whole chunks of every warp.
+// Units of at most this many nonzeros keep the dense tile in the list plan:
+// their coordinate loop is bound by the fixed latency of each evaluation, and
+// the tile ring prefetches several coordinates ahead where the lists fetch
+// one. Measured on the large corpus at r = 100 (ms per step): 117.1 with no
+// dense units in the list plan, 110.2 up to 128, 109.4 up to 256, 115.5 up to
+// 512.
+constexpr int64_t kDenseBelow = 256;
+
+// Sparse-list plan of one half: the dense buckets of the units of at most
+// kDenseBelow nonzeros, then one bucket per length class; a class's tile row
+// length is its longest unit rounded up to whole chunks of every warp.
 nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t> &ptr, int optin) {
     const int64_t units = (int64_t)ptr.size() - 1;
     const int r = c->p.r, ldr = c->ldr;
@@ -1788,8 +1809,17 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
         clusters_fit[i] = sparse_active_clusters(kSparseKinds[i], (size_t)optin);
         usable[i] = clusters_fit[i] > 0;
     }
+    for (const Bucket &d : c->plan[side]) {
+        const KernelKind &kk = kKinds[d.kind];
+        if (kk.cl == 1 && kk.k > 0 && (int64_t)kk.nt * kk.k <= kDenseBelow) {
+            Bucket b = d;
+            b.borrowed = true;
+            c->plan_sparse[side].push_back(b);
+        }
+    }
     for (int64_t u = 0; u < units; ++u) {
         const int64_t L = ptr[u + 1] - ptr[u];
+        if (L <= kDenseBelow) continue;
         const int kind = sparse_kind_for_length(L, r, ldr, optin, usable);
         lists[kind].push_back((int32_t)u);
         maxlen[kind] = std::max(maxlen[kind], L);
@@ -2037,7 +2067,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
         if (!cuda_ok(c, cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st), "reset queue"))
             return NMFKL_ECUDA;
         void *args[] = {&a};
-        const int tok = timer_begin(c, bucket_name(b));
+        const int tok = timer_begin(c, bucket_timer_name(b, side));
         cudaError_t e;
         if (b.sparse && b.cl == 1) {
             e = cudaLaunchKernel(kSparseKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
