@@ -269,12 +269,14 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
 // Register-resident groups: NT threads (32 = one warp per subproblem, several
 // per block; otherwise one CTA), K nonzeros per thread, so L <= NT*K.
 // ---------------------------------------------------------------------------
-// Minimum resident blocks per SM for the register budget: 80 registers for
-// the small warp kernels (24 warps per SM), 128 for the rest (16 warps per
-// SM) except the widest warp kernel.
+// Minimum resident blocks per SM for the register budget: 64 registers for
+// the warp kernels with K <= 2 (32 warps per SM), 80 for K = 4 (24 warps),
+// 128 for the rest (16 warps). (K = 4 at 64 and K = 8 at 80 registers spill
+// and were measured slower; so was a deeper tile ring: the warp kernels run
+// a 4-deep ring.)
 template <int NT, int K>
 __host__ __device__ constexpr int min_blocks() {
-    return NT == 32 ? (K <= 4 ? 3 : 2) : (512 / NT > 1 ? 512 / NT : 1);
+    return NT == 32 ? (K <= 2 ? 4 : (K == 4 ? 3 : 2)) : (512 / NT > 1 ? 512 / NT : 1);
 }
 // Kernel modes: one half sweep, the allocation-free F half (units are the
 // column indices themselves), and fold-in (each column runs its own sweeps of
@@ -1603,10 +1605,10 @@ struct KernelKind {
 
 constexpr int kClusterNT = 512, kClusterK = 12, kClusterD = 4;
 const KernelKind kKinds[] = {
-    {(const void *)sweep_kernel<32, 1, 8>, 32, 1, 1, 8, "sweep_warp_k1"},
-    {(const void *)sweep_kernel<32, 2, 8>, 32, 2, 1, 8, "sweep_warp_k2"},
-    {(const void *)sweep_kernel<32, 4, 8>, 32, 4, 1, 8, "sweep_warp_k4"},
-    {(const void *)sweep_kernel<32, 8, 6>, 32, 8, 1, 6, "sweep_warp_k8"},
+    {(const void *)sweep_kernel<32, 1, 4>, 32, 1, 1, 4, "sweep_warp_k1"},
+    {(const void *)sweep_kernel<32, 2, 4>, 32, 2, 1, 4, "sweep_warp_k2"},
+    {(const void *)sweep_kernel<32, 4, 4>, 32, 4, 1, 4, "sweep_warp_k4"},
+    {(const void *)sweep_kernel<32, 8, 4>, 32, 8, 1, 4, "sweep_warp_k8"},
     {(const void *)sweep_kernel<32, 16, 4>, 32, 16, 1, 4, "sweep_warp_k16"},
     {(const void *)sweep_kernel<128, 8, 8>, 128, 8, 1, 8, "sweep_cta128_k8"},
     {(const void *)sweep_kernel<256, 8, 6>, 256, 8, 1, 6, "sweep_cta256_k8"},
