@@ -83,6 +83,9 @@ typedef struct {
                              1: always the dense tile; 2: always the lists. The sums of
                              Eq. Partial are the same (terms with A_pk = 0 are zero); only
                              the FP32 summation order differs. */
+    int32_t div_mode;     /* the g/h of the projected Newton step (Section 2): 0 (default)
+                             IEEE round-to-nearest division; 1: the fast approximate
+                             division (__fdividef, 2 ulp) */
 } nmfkl_params;
 
 typedef struct nmfkl_ctx nmfkl_ctx;
@@ -201,6 +204,20 @@ nmfkl_status nmfkl_foldin(nmfkl_ctx *ctx, int64_t m_new, int64_t nnz, const int6
 /* Copies W (r x n) or F (r x m), row-major FP32, to host or device memory. */
 nmfkl_status nmfkl_get_W(nmfkl_ctx *ctx, float *out, int32_t mem_kind);
 nmfkl_status nmfkl_get_F(nmfkl_ctx *ctx, float *out, int32_t mem_kind);
+
+/* Checkpoint of Algorithm 1's state between sweeps: a self-describing blob in
+ * host memory (64-byte header: magic "NMFKLST1", version, r, n, m, seed,
+ * next sweep index; then W r x n and F r x m, row-major FP32).
+ * nmfkl_state_bytes returns its size (-1 on a NULL ctx). nmfkl_get_state
+ * writes it (EINVAL if bytes is smaller); it synchronizes. nmfkl_set_state
+ * restores W and F into a context of the same r, n, m and seed (EINVAL on a
+ * size, header or shape mismatch, with the context unchanged) and returns the
+ * stored sweep index in *next_sweep (may be NULL). Since the coordinate
+ * orders are keyed by the sweep index, nmfkl_step / nmfkl_fit from that index
+ * give bit for bit the results of the uninterrupted run. The caller owns buf. */
+int64_t nmfkl_state_bytes(const nmfkl_ctx *ctx);
+nmfkl_status nmfkl_get_state(nmfkl_ctx *ctx, int64_t next_sweep, void *buf, int64_t bytes);
+nmfkl_status nmfkl_set_state(nmfkl_ctx *ctx, const void *buf, int64_t bytes, int64_t *next_sweep);
 
 /* Reads and resets (reset != 0) the work counters. Synchronizes. */
 nmfkl_status nmfkl_get_counters(nmfkl_ctx *ctx, nmfkl_counters *out, int32_t reset);

@@ -228,6 +228,19 @@ class NMFKL:
         """F (r x m); out may be a numpy array or a CUDA tensor."""
         return self._get(self._lib.nmfkl_get_F, self.r, self.m, out)
 
+    def get_state(self, next_sweep: int) -> bytes:
+        """Checkpoint (W, F, next sweep index) as a self-describing blob."""
+        n = int(self._lib.nmfkl_state_bytes(self._h))
+        buf = ctypes.create_string_buffer(n)
+        self._check(self._lib.nmfkl_get_state(self._h, int(next_sweep), buf, n), "get_state")
+        return buf.raw
+
+    def set_state(self, blob: bytes) -> int:
+        """Restores a checkpoint of this shape and seed; returns its next sweep index."""
+        nxt = ctypes.c_int64(0)
+        self._check(self._lib.nmfkl_set_state(self._h, blob, len(blob), ctypes.byref(nxt)), "set_state")
+        return int(nxt.value)
+
     def counters(self, reset: bool = False) -> dict:
         c = Counters()
         self._check(self._lib.nmfkl_get_counters(self._h, ctypes.byref(c), int(reset)), "counters")

@@ -20,7 +20,7 @@ class Params(ctypes.Structure):
     _fields_ = [("r", c_i32), ("alpha_W", c_f64), ("beta_W", c_f64), ("alpha_F", c_f64),
                 ("beta_F", c_f64), ("eps_grad", c_f64), ("eps_div", c_f64), ("eps_x", c_f64),
                 ("max_inner", c_i32), ("grad_mode", c_i32), ("break_mode", c_i32),
-                ("perm_mode", c_i32), ("seed", c_u64), ("list_mode", c_i32)]
+                ("perm_mode", c_i32), ("seed", c_u64), ("list_mode", c_i32), ("div_mode", c_i32)]
 
 
 class Counters(ctypes.Structure):
@@ -72,6 +72,9 @@ SIGNATURES = [
                              c_i32, c_i32]),
     ("nmfkl_get_W", c_i32, [c_vp, c_vp, c_i32]),
     ("nmfkl_get_F", c_i32, [c_vp, c_vp, c_i32]),
+    ("nmfkl_state_bytes", c_i64, [c_vp]),
+    ("nmfkl_get_state", c_i32, [c_vp, c_i64, c_vp, c_i64]),
+    ("nmfkl_set_state", c_i32, [c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     ("nmfkl_get_counters", c_i32, [c_vp, ctypes.POINTER(Counters), c_i32]),
     ("nmfkl_set_timing", c_i32, [c_vp, c_i32]),
     ("nmfkl_kernel_times", c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32]),

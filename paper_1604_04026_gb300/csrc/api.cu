@@ -158,7 +158,7 @@ nmfkl_status nmfkl_create(const nmfkl_params *p, int64_t n, int64_t m, int32_t d
     if (!p || p->r < 1 || p->r > kMaxR || n < 1 || m < 1 || n > INT32_MAX || m > INT32_MAX ||
         !(p->eps_x >= 0) || p->max_inner < 0 || !(p->eps_div >= 0) || !(p->eps_grad >= 0) ||
         p->alpha_W < 0 || p->alpha_F < 0 || p->beta_W < 0 || p->beta_F < 0 || p->list_mode < 0 ||
-        p->list_mode > 2)
+        p->list_mode > 2 || p->div_mode < 0 || p->div_mode > 1)
         return NMFKL_EINVAL;
     nmfkl_ctx *c = new (std::nothrow) nmfkl_ctx();
     if (!c) return NMFKL_ENOMEM;
@@ -659,6 +659,48 @@ nmfkl_status nmfkl_get_W(nmfkl_ctx *c, float *out, int32_t mem_kind) {
 }
 nmfkl_status nmfkl_get_F(nmfkl_ctx *c, float *out, int32_t mem_kind) {
     return c ? get_factor(c, c->Ft, c->m, out, mem_kind) : NMFKL_EINVAL;
+}
+
+// Checkpoint blob: header of eight 64-bit words, then W and F row-major.
+namespace {
+constexpr uint64_t kStateMagic = 0x3154534c4b464d4eull;  // "NMFKLST1" little-endian
+constexpr uint64_t kStateVersion = 1;
+constexpr int64_t kStateHeader = 64;
+}  // namespace
+
+int64_t nmfkl_state_bytes(const nmfkl_ctx *c) {
+    if (!c) return -1;
+    return kStateHeader + (int64_t)sizeof(float) * c->p.r * (c->n + c->m);
+}
+
+nmfkl_status nmfkl_get_state(nmfkl_ctx *c, int64_t next_sweep, void *buf, int64_t bytes) {
+    if (!c || !buf || bytes < nmfkl_state_bytes(c) || next_sweep < 0) return NMFKL_EINVAL;
+    uint64_t h[8] = {kStateMagic, kStateVersion, (uint64_t)c->p.r, (uint64_t)c->n,
+                     (uint64_t)c->m, c->p.seed, (uint64_t)next_sweep, 0};
+    unsigned char *b = static_cast<unsigned char *>(buf);
+    std::memcpy(b, h, sizeof(h));
+    float *W = reinterpret_cast<float *>(b + kStateHeader);
+    float *F = W + (int64_t)c->p.r * c->n;
+    nmfkl_status st = get_factor(c, c->Wt, c->n, W, 0);
+    if (st == NMFKL_OK) st = get_factor(c, c->Ft, c->m, F, 0);
+    return st;
+}
+
+nmfkl_status nmfkl_set_state(nmfkl_ctx *c, const void *buf, int64_t bytes, int64_t *next_sweep) {
+    if (!c || !buf || bytes != nmfkl_state_bytes(c)) return NMFKL_EINVAL;
+    uint64_t h[8];
+    std::memcpy(h, buf, sizeof(h));
+    if (h[0] != kStateMagic || h[1] != kStateVersion || h[2] != (uint64_t)c->p.r || h[3] != (uint64_t)c->n ||
+        h[4] != (uint64_t)c->m || h[5] != c->p.seed || h[6] > (uint64_t)INT64_MAX) {
+        c->err = "set_state: header does not match this context";
+        return NMFKL_EINVAL;
+    }
+    const unsigned char *b = static_cast<const unsigned char *>(buf);
+    const float *W = reinterpret_cast<const float *>(b + kStateHeader);
+    const float *F = W + (int64_t)c->p.r * c->n;
+    nmfkl_status st = nmfkl_init(c, W, F, 0);
+    if (st == NMFKL_OK && next_sweep) *next_sweep = (int64_t)h[6];
+    return st;
 }
 
 nmfkl_status nmfkl_get_counters(nmfkl_ctx *c, nmfkl_counters *out, int32_t reset) {

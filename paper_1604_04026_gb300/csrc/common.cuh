@@ -67,6 +67,7 @@ struct HalfArgs {
     int32_t r, ldr;
     float alpha, beta, eps_grad, eps_div, eps_x;
     int32_t max_inner, grad_mode, break_mode, perm_mode;
+    int32_t div_mode;  // 0: IEEE division in the Newton step, 1: fast division
     uint64_t seed;
     int64_t sweep;
     int32_t side;

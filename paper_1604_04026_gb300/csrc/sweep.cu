@@ -247,7 +247,7 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
         }
         float xn;
         if (h > 0.f) {
-            xn = xk - __fdiv_rn(g, h);
+            xn = xk - (a.div_mode == 0 ? __fdiv_rn(g, h) : __fdividef(g, h));
             if (xn < 0.f) xn = 0.f;
         } else {
             xn = g > 0.f ? 0.f : xk;
@@ -2029,6 +2029,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
     a.max_inner = c->p.max_inner;
     a.grad_mode = c->p.grad_mode;
     a.break_mode = c->p.break_mode;
+    a.div_mode = c->p.div_mode;
     a.perm_mode = c->p.perm_mode;
     a.seed = c->p.seed;
     a.sweep = sweep;
@@ -2159,6 +2160,7 @@ HalfArgs fold_args(nmfkl_ctx *c, FoldState &f, bool with_ids, double rel_tol, in
     a.max_inner = c->p.max_inner;
     a.grad_mode = c->p.grad_mode;
     a.break_mode = c->p.break_mode;
+    a.div_mode = c->p.div_mode;
     a.perm_mode = c->p.perm_mode;
     a.seed = c->p.seed;
     a.side = 0;
@@ -2466,6 +2468,7 @@ extern "C" nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, 
     a.max_inner = p->max_inner;
     a.grad_mode = p->grad_mode;
     a.break_mode = p->break_mode;
+    a.div_mode = p->div_mode;
     a.perm_mode = p->perm_mode;
     a.seed = p->seed;
     a.sweep = sweep;

@@ -58,3 +58,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 def test_built_for_sm103a_only():
     flags = " ".join(_build.ARCH)
     assert "compute_103a" in flags and "sm_103a" in flags
+
+
+def test_checkpoint_entry_points_reject_null(lib):
+    """The checkpoint calls validate their arguments before touching a device."""
+    l = _native.load()
+    assert l.nmfkl_state_bytes(None) == -1
+    assert l.nmfkl_get_state(None, 0, None, 0) == 1
+    assert l.nmfkl_set_state(None, None, 0, None) == 1
+
+
+def test_params_layout_has_div_mode(lib):
+    p = _native.Params()
+    _native.load().nmfkl_default_params(ctypes.byref(p), 8)
+    assert p.div_mode == 0 and p.list_mode == 0

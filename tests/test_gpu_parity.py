@@ -441,3 +441,52 @@ def test_list_rows_beyond_clusters():
     Wo, _ = oracle.half_W(V, W0, F0, 9, 0, cfg_for(p, 1), threads=8)
     dev, _ = fp32_sensitivity(V, W0, F0, 1, p, Wo)
     assert within(Wg, Wo, slack=PROBE_FACTOR * dev).all()
+
+
+def test_checkpoint_resume_is_bit_exact(docs_small):
+    """Algorithm 1 stopped after three sweeps, saved, restored into a fresh
+    context and continued gives the uninterrupted run's W and F bit for bit
+    (the coordinate orders are keyed by the sweep index); a blob of another
+    shape, seed or size is refused and leaves the context as it was."""
+    V = docs_small
+    r = 20
+    p = params(r, seed=13)
+    with nk.NMFKL(V.n, V.m, params=p) as a:
+        a.set_data(V)
+        a.init()
+        for s in range(3):
+            a.step(s)
+        blob = a.get_state(3)
+        for s in range(3, 5):
+            a.step(s)
+        Wa, Fa = a.get_W(), a.get_F()
+    with nk.NMFKL(V.n, V.m, params=p) as b:
+        b.set_data(V)
+        b.init()
+        W0 = b.get_W()
+        with pytest.raises(nk.NMFKLError):
+            b.set_state(blob[:-4])
+        bad = bytearray(blob)
+        bad[0] ^= 1
+        with pytest.raises(nk.NMFKLError):
+            b.set_state(bytes(bad))
+        assert np.array_equal(b.get_W(), W0)
+        nxt = b.set_state(blob)
+        assert nxt == 3
+        for s in range(nxt, 5):
+            b.step(s)
+        assert np.array_equal(b.get_W(), Wa) and np.array_equal(b.get_F(), Fa)
+    with nk.NMFKL(V.n, V.m, params=params(r, seed=14)) as c:
+        c.set_data(V)
+        with pytest.raises(nk.NMFKLError):
+            c.set_state(blob)
+
+
+@pytest.mark.parametrize("list_mode", LIST_MODES)
+def test_fast_division_halves_tight(docs_small, list_mode):
+    """div_mode 1 (fast approximate division in the Newton step) meets the
+    same per-entry bar in tight mode."""
+    V, r = docs_small, 16
+    W0, F0 = start(V, r, seed=7)
+    p = params(r, seed=11, list_mode=list_mode, div_mode=1, **TIGHT)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
