@@ -1005,6 +1005,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 // in shared memory, or for giant units in the scratch slot.
 // Warp w of the group owns the chunks of 32 nonzeros c = w, w + NW, ...; its
 // lists hold only its own nonzeros, so warps never touch each other's state.
+// (In a cluster each CTA does the same on its own slice of the unit.)
 // ---------------------------------------------------------------------------
 // list entries per lane prefetched into registers: warp groups, CTA groups
 constexpr int kSparseE = 4, kSparseECta = 8;

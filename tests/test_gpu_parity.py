@@ -32,7 +32,7 @@ LIST_MODES = [1, 2]
 
 BUCKET_LENGTHS = [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513,
                   1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 12000,
-                  22527, 22528, 22529, 23041]
+                  16383, 16384, 16385, 23041]
 
 
 @pytest.fixture(scope="module")
@@ -171,8 +171,9 @@ def test_designed_lengths_reach_every_list_class(designed):
 @pytest.mark.parametrize("list_mode", LIST_MODES)
 def test_halves_tight_every_bucket(designed, list_mode):
     """Unit lengths 0..23041 around every bucket edge (warp K=1..16, CTA,
-    clusters, giant; sparse-list sub-warp, warp, CTA and cluster classes; at
-    r = 16 the 512-thread shared-state list class ends at 22,528)."""
+    clusters, giant; the dense buckets the list plan keeps, then the list
+    warp, CTA and cluster classes; the 512-thread list class ends at 16,384
+    nonzeros)."""
     V = designed
     r = 16
     W0, F0 = start(V, r, seed=2)
