@@ -151,8 +151,10 @@ __device__ __forceinline__ Staged stage_lane(const HalfArgs &a, float *tile, con
     float acc = 0.f;
     int cnt = 0;
     // The row is read kStageBatch 16-byte pieces at a time, all issued before
-    // the first is used, so that many gathers are in flight per lane.
-    constexpr int kStageBatch = 8;
+    // the first is used, so that several gathers are in flight per lane. (8 at
+    // a time measured slower: 108.8 vs 103.8 ms per step; the wider batch
+    // costs registers the coordinate loop needs, and spills at K = 16.)
+    constexpr int kStageBatch = 4;
     for (int f0 = 0; f0 < nf4; f0 += kStageBatch) {
         float4 buf[kStageBatch];
 #pragma unroll
