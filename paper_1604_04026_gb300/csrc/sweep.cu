@@ -1790,6 +1790,27 @@ void free_plan(nmfkl_ctx *c) {
 
 namespace {
 
+// Units in decreasing length, equal lengths in increasing unit id (the order
+// the persistent kernels take them in), by a counting sort on the length.
+std::vector<int32_t> order_by_length(const std::vector<int64_t> &ptr) {
+    const int64_t units = (int64_t)ptr.size() - 1;
+    int64_t max_len = 0;
+    for (int64_t u = 0; u < units; ++u) max_len = std::max(max_len, ptr[u + 1] - ptr[u]);
+    std::vector<int32_t> order(units);
+    if (max_len > (int64_t)1 << 26) {  // a count array that large: compare instead
+        for (int64_t u = 0; u < units; ++u) order[u] = (int32_t)u;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            return (ptr[x + 1] - ptr[x]) > (ptr[y + 1] - ptr[y]);
+        });
+        return order;
+    }
+    std::vector<int64_t> start(max_len + 2, 0);
+    for (int64_t u = 0; u < units; ++u) start[max_len - (ptr[u + 1] - ptr[u]) + 1]++;
+    for (int64_t i = 1; i <= max_len + 1; ++i) start[i] += start[i - 1];
+    for (int64_t u = 0; u < units; ++u) order[start[max_len - (ptr[u + 1] - ptr[u])]++] = (int32_t)u;
+    return order;
+}
+
 // Units of at most this many nonzeros keep the dense tile in the list plan:
 // their coordinate loop is bound by the fixed latency of each evaluation, and
 // the tile ring prefetches several coordinates ahead where the lists fetch
@@ -1801,7 +1822,8 @@ constexpr int64_t kDenseBelow = 256;
 // Sparse-list plan of one half: the dense buckets of the units of at most
 // kDenseBelow nonzeros, then one bucket per length class; a class's tile row
 // length is its longest unit rounded up to whole chunks of every warp.
-nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t> &ptr, int optin) {
+nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t> &ptr,
+                              const std::vector<int32_t> &order, int optin) {
     const int64_t units = (int64_t)ptr.size() - 1;
     const int r = c->p.r, ldr = c->ldr;
     std::vector<std::vector<int32_t>> lists(kNumSparseKinds);
@@ -1822,20 +1844,25 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
             c->plan_sparse[side].push_back(b);
         }
     }
-    for (int64_t u = 0; u < units; ++u) {
+    // in decreasing length, so each class's list comes out longest first; the
+    // class of a length is looked up once per distinct length
+    int64_t last_len = -1;
+    int kind = 0;
+    for (int32_t u : order) {
         const int64_t L = ptr[u + 1] - ptr[u];
-        if (L <= kDenseBelow) continue;
-        const int kind = sparse_kind_for_length(L, r, ldr, optin, usable);
-        lists[kind].push_back((int32_t)u);
+        if (L <= kDenseBelow) break;
+        if (L != last_len) {
+            kind = sparse_kind_for_length(L, r, ldr, optin, usable);
+            last_len = L;
+        }
+        lists[kind].push_back(u);
         maxlen[kind] = std::max(maxlen[kind], L);
         nnz[kind] += L;
     }
+    (void)units;
     for (int kind = 0; kind < kNumSparseKinds; ++kind) {
         auto &lst = lists[kind];
         if (lst.empty()) continue;
-        std::stable_sort(lst.begin(), lst.end(), [&](int32_t x, int32_t y) {
-            return (ptr[x + 1] - ptr[x]) > (ptr[y + 1] - ptr[y]);
-        });
         const SparseKind &sk = kSparseKinds[kind];
         const bool smem_state = sk.smem;
         const bool cta = sk.nt > 32;
@@ -1920,10 +1947,11 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
     }
     std::vector<std::vector<int32_t>> lists(kNumKinds);
     std::vector<int64_t> maxlen(kNumKinds, 0), nnz(kNumKinds, 0);
-    for (int64_t u = 0; u < units; ++u) {
+    const std::vector<int32_t> order = order_by_length(ptr);
+    for (int32_t u : order) {  // each class's list comes out longest first
         const int64_t L = ptr[u + 1] - ptr[u];
         const int kind = kind_for_length(L, usable);
-        lists[kind].push_back((int32_t)u);
+        lists[kind].push_back(u);
         maxlen[kind] = std::max(maxlen[kind], L);
         nnz[kind] += L;
     }
@@ -1934,9 +1962,6 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
     for (int kind = 0; kind < kNumKinds; ++kind) {
         auto &lst = lists[kind];
         if (lst.empty()) continue;
-        std::stable_sort(lst.begin(), lst.end(), [&](int32_t x, int32_t y) {
-            return (ptr[x + 1] - ptr[x]) > (ptr[y + 1] - ptr[y]);
-        });
         Bucket b{};
         b.kind = kind;
         b.nt = kKinds[kind].nt;
@@ -2005,7 +2030,7 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
         c->plan[side].push_back(b);
         c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
     }
-    return plan_side_sparse(c, side, ptr, optin);
+    return plan_side_sparse(c, side, ptr, order, optin);
 }
 
 nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
