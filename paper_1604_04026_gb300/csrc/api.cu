@@ -229,8 +229,12 @@ nmfkl_status nmfkl_set_data(nmfkl_ctx *c, int64_t nnz, const int64_t *colptr, co
     std::vector<int64_t> h_rowptr;
     std::vector<int32_t> h_colidx;
     std::vector<float> h_rval;
+    // Host inputs with both layouts are validated on the device after the copy
+    // (one warp per unit); the host CSR build below indexes by row, so a lone
+    // CSC is checked on the host first.
+    const bool check_on_device = mem_kind == 1 || rowptr != nullptr;
     if (mem_kind == 0) {
-        if (!check_host(c, m, n, nnz, colptr, rowidx, val, "CSC")) return NMFKL_EINVAL;
+        if (!rowptr && !check_host(c, m, n, nnz, colptr, rowidx, val, "CSC")) return NMFKL_EINVAL;
         if (!rowptr) {
             // CSR by a counting sort of the CSC (order within rows stays sorted)
             h_rowptr.assign(n + 1, 0);
@@ -248,7 +252,8 @@ nmfkl_status nmfkl_set_data(nmfkl_ctx *c, int64_t nnz, const int64_t *colptr, co
             rowptr = h_rowptr.data();
             colidx = h_colidx.data();
             rval = h_rval.data();
-        } else if (!check_host(c, n, m, nnz, rowptr, colidx, rval, "CSR")) {
+        } else if (nnz > 0 && (!colidx || !rval)) {
+            c->err = "set_data: CSR arrays missing";
             return NMFKL_EINVAL;
         }
     } else if (!rowptr || (nnz > 0 && (!colidx || !rval))) {
@@ -275,24 +280,25 @@ nmfkl_status nmfkl_set_data(nmfkl_ctx *c, int64_t nnz, const int64_t *colptr, co
         return NMFKL_ECUDA;
     }
     c->nnz = nnz;
-    if (mem_kind == 1) {
-        // device inputs: validate on the device
+    if (check_on_device) {
         int32_t *flag = c->err_flag;
         int32_t h = 0;
         ok = cuda_ok(c, cudaMemsetAsync(flag, 0, 4, c->stream), "flag") &&
-             launch_validate(c, m, n, c->colptr, c->rowidx, c->val, flag) == NMFKL_OK &&
-             launch_validate(c, n, m, c->rowptr, c->colidx, c->rval, flag) == NMFKL_OK &&
+             launch_validate(c, m, n, nnz, c->colptr, c->rowidx, c->val, flag) == NMFKL_OK &&
+             launch_validate(c, n, m, nnz, c->rowptr, c->colidx, c->rval, flag) == NMFKL_OK &&
              cuda_ok(c, cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, c->stream), "flag copy") &&
              cuda_ok(c, cudaStreamSynchronize(c->stream), "validate sync");
         if (!ok) {
             free_data(c);
             return NMFKL_ECUDA;
         }
-        int64_t last[2] = {0, 0};
+        int64_t first[2] = {0, 0}, last[2] = {0, 0};
+        cudaMemcpy(&first[0], c->colptr, 8, cudaMemcpyDeviceToHost);
+        cudaMemcpy(&first[1], c->rowptr, 8, cudaMemcpyDeviceToHost);
         cudaMemcpy(&last[0], c->colptr + m, 8, cudaMemcpyDeviceToHost);
         cudaMemcpy(&last[1], c->rowptr + n, 8, cudaMemcpyDeviceToHost);
         cudaMemsetAsync(flag, 0, 4, c->stream);
-        if (h != 0 || last[0] != nnz || last[1] != nnz) {
+        if (h != 0 || first[0] != 0 || first[1] != 0 || last[0] != nnz || last[1] != nnz) {
             c->err = "set_data: device input failed validation (offsets, sorted in-range indices, values > 0)";
             free_data(c);
             return NMFKL_EINVAL;
@@ -519,7 +525,7 @@ nmfkl_status foldin_impl(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_t
         int32_t h = 0;
         int64_t last = 0;
         ok = cuda_ok(c, cudaMemsetAsync(c->err_flag, 0, 4, c->stream), "flag") &&
-             launch_validate(c, m_new, c->n, f.colptr, f.rowidx, f.val, c->err_flag) == NMFKL_OK &&
+             launch_validate(c, m_new, c->n, nnz, f.colptr, f.rowidx, f.val, c->err_flag) == NMFKL_OK &&
              cuda_ok(c, cudaMemcpyAsync(&h, c->err_flag, 4, cudaMemcpyDeviceToHost, c->stream), "flag copy") &&
              cuda_ok(c, cudaMemcpyAsync(&last, f.colptr + m_new, 8, cudaMemcpyDeviceToHost, c->stream), "nnz copy") &&
              cuda_ok(c, cudaStreamSynchronize(c->stream), "validate sync") &&

@@ -184,24 +184,31 @@ __global__ void from_unit_major_kernel(const float *src, float *dst, int r, int6
 
 // flag bit 1: offsets not monotone or out of [0, nnz]; 2: index out of range
 // or not strictly increasing; 4: value not finite or <= 0.
-__global__ void validate_kernel(int64_t units, int64_t extent, const int64_t *ptr, const int32_t *idx,
-                                const float *val, int32_t *flag) {
-    const int64_t nnz = ptr[units];
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
-         u += (int64_t)gridDim.x * blockDim.x) {
+// One warp per unit, lanes over its entries (coalesced; a unit of any length
+// costs its entries / 32 steps): offsets in [0, nnz] and non-decreasing (flag
+// 1), indices in [0, extent) and strictly increasing within the unit (2),
+// values finite and > 0 (4).
+__global__ void validate_kernel(int64_t units, int64_t extent, int64_t nnz, const int64_t *ptr,
+                                const int32_t *idx, const float *val, int32_t *flag) {
+    // nnz is the caller's count (the size of idx and val), not ptr[units]:
+    // offsets past it are refused before any entry is read
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += warps) {
         const int64_t b = ptr[u], e = ptr[u + 1];
         if (b > e || b < 0 || e > nnz) {
-            atomicOr(flag, 1);
+            if (lane == 0) atomicOr(flag, 1);
             continue;
         }
-        int32_t prev = -1;
-        for (int64_t p = b; p < e; ++p) {
+        int bad = 0;
+        for (int64_t p = b + lane; p < e; p += 32) {
             const int32_t i = idx[p];
-            if (i <= prev || i >= extent) atomicOr(flag, 2);
-            prev = i;
+            if (i < 0 || i >= extent || (p > b && idx[p - 1] >= i)) bad |= 2;
             const float v = val[p];
-            if (!(v > 0.f) || !isfinite(v)) atomicOr(flag, 4);
+            if (!(v > 0.f) || !isfinite(v)) bad |= 4;
         }
+        bad = __reduce_or_sync(0xffffffffu, bad);
+        if (lane == 0 && bad) atomicOr(flag, bad);
     }
 }
 
@@ -353,9 +360,9 @@ void launch_density(cudaStream_t st, const float *At, int64_t rows, int ldr, int
     density_kernel<<<1024, 256, 0, st>>>(At, rows, ldr, r, ptr, out);
 }
 
-nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, const int64_t *ptr,
+nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, int64_t nnz, const int64_t *ptr,
                              const int32_t *idx, const float *val, int32_t *flag) {
-    validate_kernel<<<256, 256, 0, c->stream>>>(units, extent, ptr, idx, val, flag);
+    validate_kernel<<<4 * c->num_sms, 256, 0, c->stream>>>(units, extent, nnz, ptr, idx, val, flag);
     return cuda_ok(c, cudaGetLastError(), "validate") ? NMFKL_OK : NMFKL_ECUDA;
 }
 

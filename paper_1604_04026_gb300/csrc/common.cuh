@@ -244,7 +244,7 @@ void free_fold(nmfkl_ctx *c);
 // ptr[i+1] - ptr[i], into *out (zeroed by the caller).
 void launch_density(cudaStream_t st, const float *At, int64_t rows, int ldr, int r, const int64_t *ptr,
                     unsigned long long *out);
-nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, const int64_t *ptr,
+nmfkl_status launch_validate(nmfkl_ctx *c, int64_t units, int64_t extent, int64_t nnz, const int64_t *ptr,
                              const int32_t *idx, const float *val, int32_t *flag);
 
 }  // namespace nmfkl
