@@ -167,11 +167,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, half, workload, r):
-    """DRAM bytes per launch of `kernel` on `half` ("F" or "W") from the
-    committed ncu summary, or None when the summary is absent or the kernel
-    source changed since."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+def ncu_traffic(kernel, half, r, bucket_nnz):
+    """DRAM bytes of one launch of `kernel` on `half` ("F" or "W"), or None.
+
+    The figure comes from a small committed capture (one kernel, at most three
+    launches, on the document-like corpus; profiles/dram_traffic_small.json):
+    its DRAM bytes per nonzero of the captured bucket, times the nonzeros of
+    this workload's bucket. Traffic of these kernels grows in proportion to
+    the nonzeros they process (each nonzero's row is gathered once and its
+    list entries written and read once). None when the summary is absent, is
+    for another kernel or r, or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_small.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -179,8 +185,9 @@ def ncu_traffic(kernel, half, workload, r):
         return None
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    entry = d.get("kernels", {}).get("%s/%s/%s/r%d" % (workload, kernel, half, r))
-    return None if entry is None else entry.get("dram_bytes_per_launch_full")
+    if d.get("kernel") != "%s/%s" % (kernel, half) or d.get("r") != r:
+        return None
+    return d["dram_bytes_per_nnz"] * bucket_nnz
 
 
 def make_corpus(args, threads):
@@ -329,7 +336,7 @@ def run_ours(args):
     # plan has every unit of its half)
     step_bytes = sum(algorithmic_bytes(b["nnz"], b["count"], r) for b in plan_all if not b["list_plan"])
     ms_step = ms / args.steps
-    traffic = ncu_traffic(dom_kernel, dom_half, args.workload, r)
+    traffic = ncu_traffic(dom_kernel, dom_half, r, dom_bucket["nnz"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)",

@@ -135,13 +135,24 @@ nmfkl_status nmfkl_init(nmfkl_ctx *ctx, const float *W0, const float *F0, int32_
 
 /* One F half of Algorithm 1 (sweep index `sweep`): sumW = W 1, then every
  * column j of F is updated by Algorithm 2 on (V_j, W^T, sumW, F_j, a2, b2,
- * ids(seed, sweep, side 0, j)). Asynchronous on the context stream. */
+ * ids(seed, sweep, side 0, j)). Synchronizes the context stream at the end
+ * to read the device error flags: ETIMEOUT when a bounded wait between the
+ * CTAs of a thread-block cluster gave up (that half's results are not
+ * meaningful; the context stays usable), ENUMERIC when a NaN was written to
+ * F (e.g. from a NaN in W or F). */
 nmfkl_status nmfkl_sweep_F(nmfkl_ctx *ctx, int64_t sweep);
 
 /* One W half of Algorithm 1: sumF = F 1, then every row i of W by Algorithm
  * 2 on (V_i^T, F^T, sumF, W_i, a1, b1, ids(seed, sweep, side 1, i)).
- * Asynchronous on the context stream. */
+ * Synchronizes and reports the device error flags as nmfkl_sweep_F. */
 nmfkl_status nmfkl_sweep_W(nmfkl_ctx *ctx, int64_t sweep);
+
+/* Limit of every bounded device wait of the context's kernels (a CTA of a
+ * thread-block cluster waiting for its peers' partial sums), in SM clock
+ * cycles; 0 restores the default (4e9, about 2 s). A wait that reaches the
+ * limit makes the half return ETIMEOUT. Meant for tests of that path: a
+ * limit of a few cycles makes the waits give up. EINVAL if cycles < 0. */
+nmfkl_status nmfkl_set_wait_limit(nmfkl_ctx *ctx, int64_t cycles);
 
 /* Eq. 1 at the current W, F into *kl (FP64 accumulation; zero entries of V
  * contribute x_ij, summed in closed form as sumW . sumF) and the Eq. 2
@@ -154,7 +165,9 @@ nmfkl_status nmfkl_objective(nmfkl_ctx *ctx, double *kl, double *reg);
  * |D_s - D_{s-1}| <= rel_tol * D_{s-1} or
  * max_sweeps. kl_trace (host, max_sweeps doubles, may be NULL) receives
  * Eq. 1 after each sweep; *sweeps_done (may be NULL) the count. Returns
- * ENOTCONV when max_sweeps ran out first and rel_tol > 0. */
+ * ENOTCONV when max_sweeps ran out first and rel_tol > 0; stops at the first
+ * sweep whose device error flags or objective report ETIMEOUT or ENUMERIC
+ * (as nmfkl_sweep_F). */
 nmfkl_status nmfkl_fit(nmfkl_ctx *ctx, int64_t sweep0, int32_t max_sweeps, double rel_tol,
                        double *kl_trace, int32_t *sweeps_done);
 
@@ -162,7 +175,8 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *ctx, int64_t sweep0, int32_t max_sweeps, doubl
  * then Eq. 1 into *kl (may be NULL) for Algorithm 1's convergence test.
  * The objective is fused into the W half: each row's data term is summed
  * from its final model values, then sumW . sumF is added (FP64).
- * Synchronizes (the objective is read back). */
+ * Synchronizes (the objective is read back) and reports the device error
+ * flags as nmfkl_sweep_F; ENUMERIC also when the objective is not finite. */
 nmfkl_status nmfkl_step(nmfkl_ctx *ctx, int64_t sweep, double *kl);
 
 /* Fold-in: F for m_new new documents (columns of a new V', n x m_new)
@@ -268,27 +282,37 @@ nmfkl_status nmfkl_debug_perm(nmfkl_ctx *ctx, int64_t sweep, int32_t side, int64
  * with static storage in the library, which every GPU that loads the
  * library holds until the process exits.
  *
- * Does what nmfkl_sweep_F does for one F half (sumW = W 1, then Algorithm 2
- * on every column with ids(seed, sweep, side 0, column)), on buffers the
- * caller owns, all device memory of the current device:
- *   colptr int64[m+1], rowidx int32[nnz], val float[nnz]: CSC of V (n x m),
- *     indices sorted, values > 0;
+ * Runs the same per-column coordinate update as nmfkl_sweep_F (column sums
+ * of W, then every column j with the order keyed by (seed, sweep, side 0,
+ * j)), on buffers the caller owns, all device memory of the current device:
+ *   colptr int64[m+1]: non-decreasing, colptr[0] = 0, colptr[m] = nnz;
+ *   rowidx int32[nnz]: 0 <= rowidx < n, strictly increasing per column;
+ *   val float[nnz]: finite, > 0;
  *   Wt float[n * ldr]: W unit-major (row i holds W[0..r-1, i]), ldr =
- *     4 * ceil(r / 4), padding entries 0;
- *   Ft float[m * ldr]: F unit-major, read as the start and overwritten.
+ *     4 * ceil(r / 4), padding entries (k >= r) 0;
+ *   Ft float[m * ldr]: F unit-major, padding entries 0, read as the start
+ *     and overwritten.
+ * These preconditions are not checked: an index out of range reads out of
+ * bounds, and nonzero padding or bad values give wrong results or NaN
+ * (reported as ENUMERIC).
  * Parameters as in nmfkl_params (side F: alpha_F, beta_F; list_mode is
- * ignored: this path always runs the dense-tile warp kernels). max_len bounds
- * the nonzeros of every column; limits: r <= 256 and max_len <= 256 (EINVAL
- * beyond them; a column longer than max_len is reported as EINVAL after the
- * launch and left unchanged). Synchronizes `stream` (a cudaStream_t or NULL)
- * to read its error flags.
+ * ignored: this path always runs the dense-tile warp kernels).
+ * max_len, the longest column the caller expects, selects the kernel: the
+ * one that holds 32, 64, 128 or 256 nonzeros per column, the smallest that
+ * holds max_len. Limits: r <= 256 and max_len <= 256 (EINVAL beyond them,
+ * before any launch). A column longer than the selected kernel's capacity is
+ * left unchanged and the call returns EINVAL after the launch; a column
+ * between max_len and that capacity is updated normally. Synchronizes
+ * `stream` (a cudaStream_t or NULL) to read its error flags.
  *
  * The first call on a device takes the scratch array's device address
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture. Every call shares the one array and leaves its
- * contents behind; the work counter it needs at zero is cleared at the start
- * of each call. Calls whose work overlaps on the GPU (other streams, other
- * host threads) race on the scratch and must be serialized by the caller. */
+ * (cudaGetSymbolAddress with that device current) and keeps it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * call this entry point after a cudaDeviceReset of that device. Every call
+ * shares the one array and leaves its contents behind; the work counter it
+ * needs at zero is cleared at the start of each call. Calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the
+ * scratch and must be serialized by the caller. */
 nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, int64_t m, int32_t max_len,
                                    const int64_t *colptr, const int32_t *rowidx, const float *val,
                                    const float *Wt, float *Ft, int64_t sweep, void *stream);

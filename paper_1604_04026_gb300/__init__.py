@@ -144,6 +144,12 @@ class NMFKL:
         self.sweep_F(sweep)
         self.sweep_W(sweep)
 
+    def set_wait_limit(self, cycles: int):
+        """Limit (SM clock cycles) of the bounded waits between cluster CTAs;
+        0 restores the default. A wait that gives up makes the half raise
+        ETIMEOUT."""
+        self._check(self._lib.nmfkl_set_wait_limit(self._h, int(cycles)), "set_wait_limit")
+
     def objective(self):
         """(Eq. 1 value, Eq. 2 regularizer) in FP64."""
         kl, reg = ctypes.c_double(), ctypes.c_double()

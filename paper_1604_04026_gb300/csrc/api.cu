@@ -359,6 +359,37 @@ nmfkl_status nmfkl_init(nmfkl_ctx *c, const float *W0, const float *F0, int32_t 
     return NMFKL_OK;
 }
 
+// Clears the device error flag before a half, step or fit.
+static nmfkl_status clear_flags(nmfkl_ctx *c) {
+    return cuda_ok(c, cudaMemsetAsync(c->err_flag, 0, sizeof(int32_t), c->stream), "clear error flag") ? NMFKL_OK
+                                                                                                     : NMFKL_ECUDA;
+}
+
+// Reads the device error flag (synchronizes the stream) and maps its bits to
+// a status: a bounded wait that gave up first (the results of that half are
+// not meaningful), then a NaN written to a factor, then a unit its kernel
+// refused.
+static nmfkl_status read_flags(nmfkl_ctx *c) {
+    int32_t flag = 0;
+    if (!cuda_ok(c, cudaMemcpyAsync(&flag, c->err_flag, sizeof(flag), cudaMemcpyDeviceToHost, c->stream),
+                 "copy error flag") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "error flag sync"))
+        return NMFKL_ECUDA;
+    if (flag & kErrTimeout) {
+        c->err = "a bounded wait on a thread-block cluster peer gave up";
+        return NMFKL_ETIMEOUT;
+    }
+    if (flag & kErrNaN) {
+        c->err = "NaN produced in a sweep";
+        return NMFKL_ENUMERIC;
+    }
+    if (flag & kErrLength) {
+        c->err = "a unit was longer than its planned kernel holds";
+        return NMFKL_EINVAL;
+    }
+    return NMFKL_OK;
+}
+
 static nmfkl_status sweep_side(nmfkl_ctx *c, int side, int64_t sweep) {
     if (!c) return NMFKL_EINVAL;
     if (!c->have_data) {
@@ -366,7 +397,10 @@ static nmfkl_status sweep_side(nmfkl_ctx *c, int side, int64_t sweep) {
         return NMFKL_EINVAL;
     }
     cudaSetDevice(c->device);
-    return run_half(c, side, sweep);
+    nmfkl_status st = clear_flags(c);
+    if (st == NMFKL_OK) st = run_half(c, side, sweep);
+    if (st == NMFKL_OK) st = read_flags(c);
+    return st;
 }
 
 nmfkl_status nmfkl_sweep_F(nmfkl_ctx *c, int64_t sweep) { return sweep_side(c, 0, sweep); }
@@ -391,7 +425,8 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *c, int64_t sweep0, int32_t max_sweeps, double 
     }
     cudaSetDevice(c->device);
     double prev = 0.0;
-    nmfkl_status st = launch_objective(c, &prev, nullptr);
+    nmfkl_status st = clear_flags(c);
+    if (st == NMFKL_OK) st = launch_objective(c, &prev, nullptr);
     if (st != NMFKL_OK) return st;
     int32_t s = 0;
     bool conv = false;
@@ -399,7 +434,15 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *c, int64_t sweep0, int32_t max_sweeps, double 
         st = run_half(c, 0, sweep0 + s);
         if (st == NMFKL_OK) st = run_half(c, 1, sweep0 + s);
         double kl = 0.0;
-        if (st == NMFKL_OK) st = launch_fused_objective(c, &kl);
+        nmfkl_status obj = NMFKL_OK;
+        if (st == NMFKL_OK) obj = launch_fused_objective(c, &kl);
+        // the device flags take precedence over a non-finite objective
+        if (st == NMFKL_OK && (obj == NMFKL_OK || obj == NMFKL_ENUMERIC)) {
+            st = read_flags(c);
+            if (st == NMFKL_OK) st = obj;
+        } else if (st == NMFKL_OK) {
+            st = obj;
+        }
         if (st != NMFKL_OK) {
             if (sweeps_done) *sweeps_done = s;
             return st;
@@ -413,12 +456,6 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *c, int64_t sweep0, int32_t max_sweeps, double 
         prev = kl;
     }
     if (sweeps_done) *sweeps_done = s;
-    int32_t flag = 0;
-    cudaMemcpy(&flag, c->err_flag, 4, cudaMemcpyDeviceToHost);
-    if (flag) {
-        c->err = "NaN produced in a sweep";
-        return NMFKL_ENUMERIC;
-    }
     return (rel_tol > 0 && !conv) ? NMFKL_ENOTCONV : NMFKL_OK;
 }
 
@@ -429,10 +466,21 @@ nmfkl_status nmfkl_step(nmfkl_ctx *c, int64_t sweep, double *kl) {
         return NMFKL_EINVAL;
     }
     cudaSetDevice(c->device);
-    nmfkl_status st = run_half(c, 0, sweep);
+    nmfkl_status st = clear_flags(c);
+    if (st == NMFKL_OK) st = run_half(c, 0, sweep);
     if (st == NMFKL_OK) st = run_half(c, 1, sweep);
-    if (st == NMFKL_OK) st = launch_fused_objective(c, kl);
-    return st;
+    if (st != NMFKL_OK) return st;
+    const nmfkl_status obj = launch_fused_objective(c, kl);
+    if (obj != NMFKL_OK && obj != NMFKL_ENUMERIC) return obj;
+    // the device flags take precedence over a non-finite objective
+    st = read_flags(c);
+    return st != NMFKL_OK ? st : obj;
+}
+
+nmfkl_status nmfkl_set_wait_limit(nmfkl_ctx *c, int64_t cycles) {
+    if (!c || cycles < 0) return NMFKL_EINVAL;
+    c->wait_cycles = cycles > 0 ? (long long)cycles : kDefaultWaitCycles;
+    return NMFKL_OK;
 }
 
 // Grows the fold-in input buffers to hold m_new columns and nnz nonzeros.

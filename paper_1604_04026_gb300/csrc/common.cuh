@@ -13,6 +13,14 @@ namespace nmfkl {
 
 constexpr int kMaxR = 256;
 
+// Device error flag bits, set by the kernels and read by the host after a half.
+constexpr int32_t kErrNaN = 1;      // a factor entry came out NaN
+constexpr int32_t kErrTimeout = 2;  // a bounded wait on a cluster peer gave up
+constexpr int32_t kErrLength = 4;   // a unit longer than its kernel's capacity was refused
+// Default limit of a bounded device wait, in SM clock cycles (~2 s at 2 GHz:
+// a wait that long means a peer is gone).
+constexpr long long kDefaultWaitCycles = 4000000000ll;
+
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): per round two 64x64 ->
 // 128-bit products of counter words 0 and 2 by fixed multipliers, output
@@ -79,7 +87,8 @@ struct HalfArgs {
     int64_t slot_floats;
     int32_t lcap;          // tile row length (max nonzeros of a unit in this bucket)
     unsigned long long *counters;  // coords, evals, steps, cap_hits
-    int32_t *err;          // device error flag
+    int32_t *err;          // device error flag (kErr* bits)
+    long long wait_cycles; // limit of each bounded wait on a cluster peer
     double *unit_obj;      // if set: per unit, sum over its nonzeros of v log(v/(x+eps)) - v
                            // at the unit's final x (Eq. 1's data term, fused into the W half)
     const int32_t *count_dev;  // if set, the bucket's unit count is read here (device-built buckets)
@@ -173,6 +182,7 @@ struct nmfkl_ctx {
     unsigned long long *counters = nullptr;
     int32_t *queues = nullptr;     // one per bucket per side
     int32_t *err_flag = nullptr;
+    long long wait_cycles = nmfkl::kDefaultWaitCycles;  // bounded device waits
     float *scratch = nullptr;
     int64_t scratch_floats = 0;
     float *tbuf = nullptr;         // transpose staging for get/set

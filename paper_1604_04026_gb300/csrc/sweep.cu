@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
         if constexpr (kMode != kModeHalf) {
             // no host-side length buckets on these paths: a unit beyond NT*K nonzeros is refused
             if (L > NT * K || L < 0) {
-                if (tid_g == 0) atomicOr(a.err, 4);
+                if (tid_g == 0) atomicOr(a.err, kErrLength);
                 continue;
             }
         }
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
         discard_tile(tile, r, L, lcap, tid_g, NT);
         for (int k = tid_g; k < r; k += NT) {
             const float xv = x_out[k];
-            if (!(xv == xv)) atomicOr(a.err, 1);
+            if (!(xv == xv)) atomicOr(a.err, kErrNaN);
             a.X[u * ldr + k] = xv;
         }
     }
@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
         __syncthreads();
         for (int k = threadIdx.x; k < r; k += kGiantNT) {
             const float xv = x_out[k];
-            if (!(xv == xv)) atomicOr(a.err, 1);
+            if (!(xv == xv)) atomicOr(a.err, kErrNaN);
             a.X[u * ldr + k] = xv;
         }
     }
@@ -728,7 +728,6 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
 // decisions. Units are assigned to clusters round-robin, longest first.
 // ---------------------------------------------------------------------------
 constexpr int kClusterMax = 16;
-constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz: a wait that long is a fault
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -822,9 +821,9 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
             if (live && lane == 0) {
                 const long long t0 = clock64();
                 while (!mbar_try_wait(my_bar, phase[par])) {
-                    if (clock64() - t0 > kWaitCycles) {
+                    if (clock64() - t0 > a.wait_cycles) {
                         s_abort = 1;
-                        atomicOr(a.err, 2);
+                        atomicOr(a.err, kErrTimeout);
                         break;
                     }
                 }
@@ -832,7 +831,11 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
             __syncwarp();
         }
         __syncthreads();
-        combine(slots + par * kClusterMax, csize);
+        // After a timeout a late peer may still store into the slots while
+        // they are read: an aborted CTA combines no slot at all, so every one
+        // of its threads gets the same (zero) total and takes the same
+        // decisions (s_abort was written before the barrier above).
+        combine(slots + par * kClusterMax, s_abort ? 0u : csize);
         phase[par] ^= 1u;
         par ^= 1;
     };
@@ -985,7 +988,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
         if (crank == 0) {
             for (int k = threadIdx.x; k < r; k += NT) {
                 const float xv = x_out[k];
-                if (!(xv == xv)) atomicOr(a.err, 1);
+                if (!(xv == xv)) atomicOr(a.err, kErrNaN);
                 a.X[u * ldr + k] = xv;
             }
         }
@@ -1146,9 +1149,9 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
     uint32_t crank = 0, csize = 1;
     unsigned long long *xslots = reinterpret_cast<unsigned long long *>(smem_raw + lay.bytes);
     unsigned long long *xbar = xslots + 2 * kClusterMax;
-    __shared__ int s_abort;
     uint32_t xphase[2] = {0u, 0u};
     int xpar = 0;
+    bool aborted = false;  // a wait of this CTA gave up (the same in every thread of the CTA)
     if constexpr (kCluster) {
         cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
         crank = cluster.block_rank();
@@ -1156,31 +1159,39 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
         if (threadIdx.x == 0) {
             mbar_init(smem_addr(&xbar[0]), csize);
             mbar_init(smem_addr(&xbar[1]), csize);
-            s_abort = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         cluster.sync();
     }
     // Sum over the cluster of one 64-bit value per CTA (`mine`, meaningful in
-    // warp 0); `combine` reads the csize slots in rank order.
+    // warp 0); `combine` reads the slots of the first n ranks in rank order.
+    // Each thread waits on its CTA's mbarrier with a bounded loop; one
+    // CTA-wide vote then decides whether any of them gave up, so all threads
+    // take the same path. An aborted CTA stops exchanging and combines no
+    // slot (a late peer may still be storing into them): its threads keep
+    // identical totals, and its peers give up on their next wait for it.
     auto cluster_sum = [&](unsigned long long mine, auto &&combine) {
         const uint32_t bar = smem_addr(&xbar[xpar]);
-        if (!*reinterpret_cast<volatile int *>(&s_abort)) {
+        if (!aborted) {
             if (warp_in_block == 0 && lane < (int)csize) {
                 const uint32_t slot = smem_addr(&xslots[xpar * kClusterMax + crank]);
                 st_cluster_u64(map_rank(slot, lane), mine);
                 mbar_arrive_remote(map_rank(bar, lane));
             }
+            bool late = false;
             const long long t0 = clock64();
             while (!mbar_try_wait(bar, xphase[xpar])) {
-                if (clock64() - t0 > kWaitCycles) {
-                    s_abort = 1;
-                    atomicOr(a.err, 2);
+                if (clock64() - t0 > a.wait_cycles) {
+                    late = true;
                     break;
                 }
             }
+            if (__syncthreads_or(late)) {
+                aborted = true;
+                if (threadIdx.x == 0) atomicOr(a.err, kErrTimeout);
+            }
         }
-        combine(xslots + xpar * kClusterMax, (int)csize);
+        combine(xslots + xpar * kClusterMax, aborted ? 0 : (int)csize);
         xphase[xpar] ^= 1u;
         xpar ^= 1;
     };
@@ -1274,7 +1285,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             L = min(Lc, L - my0);
         }
         if (Lc > lcap) {  // cannot happen with a consistent plan; refuse rather than overrun
-            if (tid_g == 0) atomicOr(a.err, 4);
+            if (tid_g == 0) atomicOr(a.err, kErrLength);
             continue;
         }
         for (int k = tid_g; k < ldr; k += GS) {
@@ -1586,7 +1597,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
         if (crank == 0) {
             for (int k = tid_g; k < r; k += GS) {
                 const float xk = x_out[k];
-                if (!(xk == xk)) atomicOr(a.err, 1);
+                if (!(xk == xk)) atomicOr(a.err, kErrNaN);
                 a.X[u * ldr + k] = xk;
             }
         }
@@ -2065,6 +2076,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
     a.scratch = c->scratch;
     a.counters = c->counters;
     a.err = c->err_flag;
+    a.wait_cycles = c->wait_cycles;
     a.unit_obj = F ? nullptr : c->unit_obj;
     // dense tile or sparse lists (list_mode): in automatic mode, the lists when
     // the fixed factor is less than half dense at the nonzeros of V
@@ -2195,6 +2207,7 @@ HalfArgs fold_args(nmfkl_ctx *c, FoldState &f, bool with_ids, double rel_tol, in
     a.scratch = f.scratch;
     a.counters = c->counters;
     a.err = f.ctl + 2 * kFoldKinds;
+    a.wait_cycles = c->wait_cycles;
     a.unit_ids = with_ids ? f.ids : nullptr;
     a.max_sweeps = max_sweeps;
     a.rel_tol = rel_tol;
@@ -2460,8 +2473,11 @@ extern "C" nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, 
     const int lcap = 32 * kk.k;
     const int64_t slot_floats = ((int64_t)r * lcap + 63) / 64 * 64;
     int optin = 0, sms = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return NMFKL_ECUDA;
+    }
     optin -= 1024;
     const size_t gbytes = ring_layout(r, ldr, 32, kk.k, kk.d, false).bytes;
     int gpb = 8;
@@ -2509,6 +2525,7 @@ extern "C" nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, 
     a.lcap = lcap;
     a.counters = ctl->counters;
     a.err = &ctl->err;
+    a.wait_cycles = kDefaultWaitCycles;
     a.unit_obj = nullptr;
     void *args[] = {&a};
     if (cudaLaunchKernel(kk.fn, dim3((unsigned)grid), dim3(32 * gpb), args, smem, st) != cudaSuccess)

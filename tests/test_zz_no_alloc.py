@@ -86,8 +86,10 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     colptr = torch.from_numpy(V.colptr).cuda()
     rowidx = torch.from_numpy(V.rowidx).cuda()
     val = torch.from_numpy(V.val).cuda()
-    Wt = torch.zeros((V.n, 8), dtype=torch.float32, device="cuda")
-    Ft = torch.zeros((V.m, 8), dtype=torch.float32, device="cuda")
+    # a nonzero start, so that a kernel writing into a refused column would show
+    Wt = _unit_major(torch, synth.uniform_init(8, V.n, 7, 0), 8)
+    Ft = _unit_major(torch, synth.uniform_init(8, V.m, 7, 1), 8)
+    F_start = Ft.clone()
     args = (colptr.data_ptr(), rowidx.data_ptr(), val.data_ptr(), Wt.data_ptr(), Ft.data_ptr(), 0, None)
     # max_len above the 256 limit
     assert lib.nmfkl_sweep_F_noalloc(ctypes.byref(p), V.n, V.m, 300, *args) == 1
@@ -95,5 +97,8 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     big = nk.default_params(8)
     big.r = 300
     assert lib.nmfkl_sweep_F_noalloc(ctypes.byref(big), V.n, V.m, 128, *args) == 1
-    # a column longer than the stated max_len is refused after the launch
+    assert torch.equal(Ft, F_start)
+    # max_len 32 selects the kernel that holds 32 nonzeros per column; every
+    # column here is longer, so each is refused after the launch and left as it was
     assert lib.nmfkl_sweep_F_noalloc(ctypes.byref(p), V.n, V.m, 32, *args) == 1
+    assert torch.equal(Ft, F_start)
