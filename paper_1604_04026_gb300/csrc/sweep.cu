@@ -819,13 +819,16 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
                 mbar_arrive_remote(map_rank(my_bar, lane));
             }
             if (live && lane == 0) {
+                // the clock is checked before every try, so a limit shorter
+                // than one clock read gives up at once
                 const long long t0 = clock64();
-                while (!mbar_try_wait(my_bar, phase[par])) {
+                for (;;) {
                     if (clock64() - t0 > a.wait_cycles) {
                         s_abort = 1;
                         atomicOr(a.err, kErrTimeout);
                         break;
                     }
+                    if (mbar_try_wait(my_bar, phase[par])) break;
                 }
             }
             __syncwarp();
@@ -1178,13 +1181,16 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                 st_cluster_u64(map_rank(slot, lane), mine);
                 mbar_arrive_remote(map_rank(bar, lane));
             }
+            // the clock is checked before every try, so a limit shorter than
+            // one clock read gives up at once
             bool late = false;
             const long long t0 = clock64();
-            while (!mbar_try_wait(bar, xphase[xpar])) {
+            for (;;) {
                 if (clock64() - t0 > a.wait_cycles) {
                     late = true;
                     break;
                 }
+                if (mbar_try_wait(bar, xphase[xpar])) break;
             }
             if (__syncthreads_or(late)) {
                 aborted = true;

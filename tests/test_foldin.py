@@ -20,7 +20,7 @@ import oracle
 import paper_1604_04026_gb300 as nk
 from paper_1604_04026_gb300 import synth
 
-from _util import PROBE_FACTOR, TIGHT, cfg_for, fp32_sensitivity, params, unit_objectives, within
+from _util import PROBE_FACTOR, TIGHT, assert_parity, cfg_for, fp32_sensitivity, params, unit_objectives
 
 pytestmark = pytest.mark.gpu
 
@@ -70,8 +70,7 @@ def test_one_pass_matches_oracle_tight(corpus):
     Fo, done = oracle.foldin(V, W, F0, p.seed, rel_tol=0.0, max_sweeps=1, c=c)
     assert (done == 1).all()
     dev, _ = fp32_sensitivity(V, W, F0, 0, p, Fo)
-    ok = within(F, Fo, slack=PROBE_FACTOR * dev)
-    assert ok.all(), (int((~ok).sum()), np.argwhere(~ok)[:5])
+    assert_parity("foldin_one_pass_tight/F", F, Fo, slack=PROBE_FACTOR * dev)
 
 
 def test_full_foldin_objective_parity(corpus):

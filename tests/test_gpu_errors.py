@@ -16,7 +16,7 @@ import oracle
 import paper_1604_04026_gb300 as nk
 from paper_1604_04026_gb300 import synth
 
-from _util import PROBE_FACTOR, TIGHT, cfg_for, fp32_sensitivity, model, params, start, within
+from _util import PROBE_FACTOR, TIGHT, assert_parity, cfg_for, fp32_sensitivity, model, params, start
 
 pytestmark = pytest.mark.gpu
 
@@ -64,7 +64,7 @@ def test_cluster_wait_limit_gives_etimeout_then_recovers(list_mode):
     m.close()
     Wo, _ = oracle.half_W(V, W0, F0, 8, 0, cfg_for(p, 1), threads=8)
     dev, _ = fp32_sensitivity(V, W0, F0, 1, p, Wo)
-    assert within(Wg, Wo, slack=PROBE_FACTOR * dev).all()
+    assert_parity("after_timeout/lm%d/W" % list_mode, Wg, Wo, slack=PROBE_FACTOR * dev)
 
 
 def test_wait_limit_rejects_negative():

@@ -10,7 +10,9 @@ from the same state:
     value, computed for all columns): sampled rows, the longest ones included.
 Bars as in the paper-constant parity tests: at least 99% of the sampled
 entries within 1e-4 relative + 1e-6 x the unit's largest entry + 4 x the
-entry's FP32 sensitivity (Monte Carlo arithmetic probes of the oracle), and
+entry's FP32 sensitivity (Monte Carlo arithmetic probes of the oracle), that
+slack capped at 10 x the plain bound; the fraction within the plain bar is
+reported beside it; and
 every sampled unit's subproblem objective within 1e-5 of the magnitude of
 its terms (+ 4 x its probe spread).
 """
@@ -21,7 +23,7 @@ import oracle
 import paper_1604_04026_gb300 as nk
 from paper_1604_04026_gb300 import synth
 
-from _util import PROBE_FACTOR, U32, cfg_for, within
+from _util import PROBE_FACTOR, U32, cfg_for, parity_report
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +57,7 @@ def _unit_scale(v, A, x, sumA, eps):
 
 def _check_sampled(units, ptr, idx, val, A_full, X0, sumA, got, p, side):
     c = cfg_for(p, side)
-    ok_all = []
+    G, O, S = [], [], []
     for u in units:
         a, b = ptr[u], ptr[u + 1]
         v = val[a:b].astype(np.float64)
@@ -72,14 +74,19 @@ def _check_sampled(units, ptr, idx, val, A_full, X0, sumA, got, p, side):
             dev = np.maximum(dev, np.abs(xp - ref))
             probe_obj.append(_unit_obj(v, A, xp, sumA, p.eps_div))
         g = got[:, u].astype(np.float64)
-        ok_all.append(within(g[:, None], ref[:, None], slack=PROBE_FACTOR * dev[:, None])[:, 0])
+        G.append(g)
+        O.append(ref)
+        S.append(PROBE_FACTOR * dev)
         d_ref = _unit_obj(v, A, ref, sumA, p.eps_div)
         spread = max(abs(x - d_ref) for x in probe_obj)
         err = abs(_unit_obj(v, A, g, sumA, p.eps_div) - d_ref)
         assert err <= 1e-5 * _unit_scale(v, A, ref, sumA, p.eps_div) + PROBE_FACTOR * spread, (side, int(u), err)
         assert (g >= 0).all()
-    frac = np.concatenate(ok_all).mean()
-    assert frac >= 0.99, (side, frac)
+    # columns are the sampled units; at the paper's constants a break or clamp
+    # decision may flip between FP32 and FP64, so the gate is a fraction
+    rep = parity_report("full_size_sampled/%s" % ("F" if side == 0 else "W"), np.stack(G, axis=1),
+                        np.stack(O, axis=1), slack=np.stack(S, axis=1))
+    assert 1.0 - rep["beyond_cap"] / rep["entries"] >= 0.99, rep
 
 
 def test_full_size_sampled_parity(large):

@@ -3,16 +3,20 @@ the same seeded inputs.
 
 Bars (FP32 path vs FP64 oracle), each half from an identical state:
   * tight mode (every coordinate solved to its 1-D minimiser): every entry
-    within 1e-4 relative + 1e-6 x the unit's largest entry + 4 x its FP32
+    within the plain bar, 1e-4 relative + 1e-6 x the unit's largest entry,
+    except at most 0.5% of the entries, which may add 4 x their FP32
     sensitivity (max over 8 Monte Carlo arithmetic runs of the oracle, see
-    fp32_sensitivity);
+    fp32_sensitivity) but never exceed 10 x the plain bound; every check
+    prints (and with PARITY_REPORT=file records) the fraction within the
+    plain bar, the entries that needed the slack and the largest error;
     the per-unit subproblem objective within 2e-6 of the magnitude of its
     terms (plus 4 x its probe spread);
   * the paper's constants (eps_x = 0.1): at least 99.5% of entries within the
-    same bar (a break or clamp decision can flip between FP32 and FP64 for
+    capped bar (a break or clamp decision can flip between FP32 and FP64 for
     an entry on its threshold), per-unit objective within 1e-5, and the KL
     trajectory over 20 sweeps within 1e-4 relative after every sweep, plus
-    4 x the spread FP32-level rounding gives the oracle's trajectory;
+    4 x the spread FP32-level rounding gives the oracle's trajectory (capped
+    at 10 x the 1e-4 bar; the plain relative error is reported);
   * integer work (coordinate orders) and the random start: bit-exact.
 """
 import numpy as np
@@ -22,8 +26,9 @@ import oracle
 import paper_1604_04026_gb300 as nk
 from paper_1604_04026_gb300 import synth
 
-from _util import (PROBE_FACTOR, RTOL, TIGHT, cfg_for, designed_matrix, fp32_sensitivity, model,
-                   objective_scale, params, start, trajectory_sensitivity, unit_objectives, within)
+from _util import (PROBE_FACTOR, RTOL, SLACK_CAP, TIGHT, assert_parity, cfg_for, designed_matrix, fp32_sensitivity,
+                   model, objective_scale, params, report_trajectory, start, trajectory_sensitivity,
+                   unit_objectives)
 
 pytestmark = pytest.mark.gpu
 
@@ -129,13 +134,11 @@ def _halves(V, W0, F0, p, threads=8):
     return Fg, Fo, Wg, Wo, F1
 
 
-def _check_halves(V, W0, F0, Fg, Fo, Wg, Wo, F1, p, fraction=1.0, obj_rel=OBJ_REL):
+def _check_halves(V, W0, F0, Fg, Fo, Wg, Wo, F1, p, fraction=None, obj_rel=OBJ_REL, name="halves"):
     for side, got, want, start_F in ((0, Fg, Fo, F0), (1, Wg, Wo, F1)):
         dev, probes = fp32_sensitivity(V, W0, start_F, side, p, want)
-        ok = within(got, want, slack=PROBE_FACTOR * dev)
-        bad = np.argwhere(~ok)
-        assert ok.mean() >= fraction, (side, ok.mean(), [(int(k), int(u), float(got[k, u]), float(want[k, u]))
-                                                           for k, u in bad[:4]])
+        assert_parity("%s/%s" % (name, "F" if side == 0 else "W"), got, want, slack=PROBE_FACTOR * dev,
+                      fraction=fraction)
         assert (got >= 0).all()
         # per-unit objective of Eq. kl, with the same probe-measured slack
         alpha, beta = (p.alpha_F, p.beta_F) if side == 0 else (p.alpha_W, p.beta_W)
@@ -178,7 +181,7 @@ def test_halves_tight_every_bucket(designed, list_mode):
     r = 16
     W0, F0 = start(V, r, seed=2)
     p = params(r, seed=5, list_mode=list_mode, **TIGHT)
-    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, name="tight_every_bucket/lm%d" % list_mode)
 
 
 @pytest.mark.parametrize("list_mode", LIST_MODES)
@@ -192,7 +195,22 @@ def test_halves_tight(case, docs_small, list_mode):
         V, r, extra = docs_small, 12, dict(alpha_W=0.5, beta_W=0.1, alpha_F=0.2, beta_F=0.3)
     W0, F0 = start(V, r, seed=7)
     p = params(r, seed=11, list_mode=list_mode, **TIGHT, **extra)
-    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, name="tight_%s/lm%d" % (case, list_mode))
+
+
+@pytest.mark.parametrize("list_mode", LIST_MODES)
+@pytest.mark.parametrize("case", ["c1", "docs_r37"])
+def test_halves_tight_eps_div_1e10(case, docs_small, list_mode):
+    """The same gate with the denominator guard at 1e-10 instead of 1e-6: x_p
+    is exactly 0 on the GPU whenever all its terms vanish (positive-term
+    count), so the smaller guard changes no computed value's meaning."""
+    if case == "c1":
+        V, r = synth.poisson_lowrank(1000, 500, 10, seed=0), 10
+    else:
+        V, r = docs_small, 37
+    W0, F0 = start(V, r, seed=7)
+    p = params(r, seed=11, list_mode=list_mode, eps_div=1e-10, **TIGHT)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, name="tight_eps_div_1e-10_%s/lm%d" % (case, list_mode))
 
 
 def test_r1_closed_form_on_gpu():
@@ -217,7 +235,7 @@ def test_r256(docs_small, list_mode):
     r = 256
     W0, F0 = start(V, r, seed=9)
     p = params(r, seed=1, list_mode=list_mode, **TIGHT)
-    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, name="tight_r256/lm%d" % list_mode)
 
 
 def test_empty_units_go_to_zero():
@@ -255,7 +273,10 @@ def test_kl_trajectory_20_sweeps(case, docs_small, list_mode):
     # measured spread (it is far below 1e-4 on most sweeps)
     spread = trajectory_sensitivity(V, W0, F0, p, 20, ref.kl)
     err = np.abs(traj - ref.kl)
-    assert (err <= RTOL * ref.kl + PROBE_FACTOR * spread).all(), (err / ref.kl, spread / ref.kl)
+    rel = err / ref.kl
+    report_trajectory("kl_trajectory_%s/lm%d" % (case, list_mode), rel, spread / ref.kl)
+    bound = np.minimum(RTOL * ref.kl + PROBE_FACTOR * spread, SLACK_CAP * RTOL * ref.kl)
+    assert (err <= bound).all(), (rel, spread / ref.kl)
     # monotone within FP32 noise
     assert (np.diff(traj) <= 1e-6 * traj[:-1]).all()
     m.close()
@@ -270,7 +291,8 @@ def test_halves_paper_constants(case, docs_small, list_mode):
     V, r = (synth.poisson_lowrank(1000, 500, 10, seed=0), 10) if case == "c1" else (docs_small, 20)
     W0, F0 = start(V, r, seed=6)
     p = params(r, seed=6, list_mode=list_mode)
-    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, fraction=0.995, obj_rel=1e-5)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, fraction=0.995, obj_rel=1e-5,
+                  name="paper_constants_%s/lm%d" % (case, list_mode))
 
 
 def test_literal_modes(docs_small):
@@ -408,7 +430,7 @@ def test_long_rows_every_cluster_size(list_mode):
     m_.close()
     Wo, _ = oracle.half_W(V, W0, F0, 8, 0, cfg_for(p, 1), threads=8)
     dev, _ = fp32_sensitivity(V, W0, F0, 1, p, Wo)
-    assert within(Wg, Wo, slack=PROBE_FACTOR * dev).all()
+    assert_parity("long_rows/lm%d/W" % list_mode, Wg, Wo, slack=PROBE_FACTOR * dev)
 
 
 def test_list_rows_beyond_clusters():
@@ -441,7 +463,7 @@ def test_list_rows_beyond_clusters():
     m_.close()
     Wo, _ = oracle.half_W(V, W0, F0, 9, 0, cfg_for(p, 1), threads=8)
     dev, _ = fp32_sensitivity(V, W0, F0, 1, p, Wo)
-    assert within(Wg, Wo, slack=PROBE_FACTOR * dev).all()
+    assert_parity("list_rows_beyond_clusters/W", Wg, Wo, slack=PROBE_FACTOR * dev)
 
 
 def test_checkpoint_resume_is_bit_exact(docs_small):
@@ -490,4 +512,4 @@ def test_fast_division_halves_tight(docs_small, list_mode):
     V, r = docs_small, 16
     W0, F0 = start(V, r, seed=7)
     p = params(r, seed=11, list_mode=list_mode, div_mode=1, **TIGHT)
-    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, name="tight_fastdiv/lm%d" % list_mode)

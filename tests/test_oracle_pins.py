@@ -384,18 +384,79 @@ def test_foldin_recovers_exact_fit():
     assert done.max() <= 3000
 
 
+def _column_objectives(V, W, F, eps_div=1e-6):
+    """Eq. kl of every column (data term over its nonzeros plus the linear
+    term sum_k sumW_k F_kj), straight from the dense products in numpy."""
+    out = np.zeros(V.m)
+    sumW = W.sum(axis=1)
+    for j in range(V.m):
+        a, b = V.colptr[j], V.colptr[j + 1]
+        v = V.val[a:b].astype(np.float64)
+        x = W[:, V.rowidx[a:b]].T @ F[:, j]
+        out[j] = np.sum(v * np.log(v / (x + eps_div)) - v) + sumW @ F[:, j]
+    return out
+
+
 def test_foldin_stops_on_relative_change():
+    """Each document stops after the first pass whose objective changed by at
+    most rel_tol times the previous value, and not before: the objectives
+    after exactly t passes (fixed pass counts, rel_tol = 0) show that the last
+    pass met the test and the one before it did not."""
     topics, V = synth.foldin_docs(500, 30, 6, seed=2, threads=2)
     W = topics.astype(np.float64)
     F0 = synth.uniform_init(6, V.m, 0, 1)
-    F, done = oracle.foldin(V, W, F0, seed=0, rel_tol=1e-5, max_sweeps=200)
+    tol = 1e-5
+    F, done = oracle.foldin(V, W, F0, seed=0, rel_tol=tol, max_sweeps=200)
     assert (done >= 1).all() and (done < 200).all()
-    # one more sweep on a finished document changes its objective by <= ~tol
+    assert (done >= 3).sum() >= V.m // 2  # most documents need several passes
+    D = []
+    for t in range(int(done.max()) + 1):
+        Ft, dt = oracle.foldin(V, W, F0, seed=0, rel_tol=0.0, max_sweeps=t)
+        # with rel_tol = 0 a document stops early only on an exactly unchanged
+        # objective (every coordinate already optimal), and stays there
+        assert (dt <= t).all()
+        D.append(_column_objectives(V, W, Ft))
+        for j in np.nonzero(done == t)[0]:
+            # the stopped result is the state after exactly `done` passes
+            assert np.array_equal(Ft[:, j], F[:, j]), j
+    D = np.array(D)  # D[t, j]: objective of document j after t passes
+    slop = 1e-12  # evaluation-order rounding between the oracle's sum and numpy's
     for j in range(V.m):
-        d0 = oracle.column_objective(V, W, F, j)
-        Fj, _ = oracle.foldin(V, W, F, seed=0, rel_tol=0.0, max_sweeps=1)
-        assert Fj.min() >= 0
-        assert d0 >= 0
+        d = int(done[j])
+        assert abs(D[d - 1, j] - D[d, j]) <= tol * abs(D[d - 1, j]) * (1 + slop) + slop * abs(D[d, j]), j
+        if d >= 2:
+            assert abs(D[d - 2, j] - D[d - 1, j]) > tol * abs(D[d - 2, j]) * (1 - slop), j
+
+
+def test_probe_magnitude_matches_first_order_closed_form():
+    """The Monte Carlo arithmetic probe perturbs each x_p by a relative
+    eps*xi, xi ~ U(-1, 1), after its initial sum. On an r = 1 column of L unit
+    counts with W = 1 on every row (S = sum W = n = L) and eps_div = 0, one
+    Newton step from f0 gives f1 = f0 + f0 (U1 - S f0) / U2 with U1 = sum
+    1/(1+d_p), U2 = sum 1/(1+d_p)^2, so to first order in the perturbations
+    d_p, df1 = f0 (L - 2 S f0) / L^2 * sum_p d_p, whose standard deviation is
+    |f0 (L - 2 S f0)| / L^2 * eps * sqrt(L / 3). The spread of the probe runs
+    must match it (a probe that over- or under-perturbs fails)."""
+    L, f0, eps = 400, 0.3, 2.0 ** -24
+    dense = np.ones((L, 1), dtype=np.float32)
+    V = synth.from_dense(dense)
+    W = np.ones((1, L))
+    F0 = np.full((1, 1), f0)
+    base = dict(eps_div=0.0, eps_x=0.0, eps_grad=0.0, max_inner=1)
+    ref, st = oracle.half_F(V, W, F0, 0, 0, oracle.cfg(**base))
+    assert st["steps"] == 1
+    S = float(L)
+    assert ref[0, 0] == pytest.approx(f0 + f0 * (L - S * f0) / L, rel=1e-14)
+    devs = []
+    for s in range(256):
+        x, _ = oracle.half_F(V, W, F0, 0, 0, oracle.cfg(perturb=eps, perturb_seed=1 + s, **base))
+        devs.append(x[0, 0] - ref[0, 0])
+    devs = np.array(devs)
+    predicted = abs(f0 * (L - 2 * S * f0)) / L ** 2 * eps * np.sqrt(L / 3.0)
+    measured = devs.std()
+    # sampling error of a standard deviation from 256 runs is ~4.4%
+    assert 0.8 * predicted <= measured <= 1.25 * predicted, (measured, predicted)
+    assert abs(devs.mean()) <= 4 * predicted / np.sqrt(len(devs))
 
 
 def test_rounding_probe_off_by_default_and_deterministic():
