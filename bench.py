@@ -323,7 +323,7 @@ def run_ours(args):
     # per half; a dense bucket the list plan keeps is the same units) over its
     # mean launch time in the timed steps
     peak, peak_kind = measured_peak_hbm()
-    sweep_kernels = {k: v for k, v in times.items() if k.startswith(("sweep_", "sparse_"))}
+    sweep_kernels = {k: v for k, v in times.items() if k.startswith(("sweep_", "sparse_", "group_"))}
     dom = max(sweep_kernels, key=lambda k: sweep_kernels[k][1])
     launches, dom_ms = sweep_kernels[dom]
     per_launch_ms = dom_ms / max(launches, 1)

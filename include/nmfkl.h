@@ -264,6 +264,48 @@ typedef struct {
 /* Fills up to `cap` entries; returns the number of buckets (-1 on a NULL ctx). */
 int32_t nmfkl_plan_info(const nmfkl_ctx *ctx, nmfkl_bucket_info *out, int32_t cap);
 
+/* Launch-plan choices (not part of the paper's method: they pick among
+ * kernels that compute the same Algorithm 2, differing only in FP32
+ * summation order):
+ *   list_threshold: with list_mode 0 a half runs the sparse-list plan when
+ *     the fixed factor's density at the nonzeros of V is below it, else the
+ *     dense-tile plan (chosen on the device before the half); default 0.5;
+ *   short_kernel[side][c]: in the list plan, for units of at most 32, 64,
+ *     128 and 256 nonzeros (c = 0..3) of the F half (side 0) or W half (side
+ *     1): 0 = the dense-tile warp kernel (default), 1 = the sub-warp group
+ *     kernel (G lanes per unit over per-coordinate lists of the compressed
+ *     factor rows). */
+typedef struct {
+    double list_threshold;
+    int32_t short_kernel[2][4];
+} nmfkl_plan_choice;
+
+/* Reads the context's choices. EINVAL on NULL arguments. */
+nmfkl_status nmfkl_get_plan_choice(const nmfkl_ctx *ctx, nmfkl_plan_choice *out);
+
+/* Sets them (EINVAL if list_threshold is not in [0, 1] or a short_kernel
+ * entry is not 0 or 1; the context is then unchanged). Takes effect at the
+ * next half; the captured step graph is rebuilt. */
+nmfkl_status nmfkl_set_plan_choice(nmfkl_ctx *ctx, const nmfkl_plan_choice *in);
+
+/* Autotuner of the launch plan. From the context's current W and F (both
+ * restored afterwards, so tuning changes no result), runs each half `reps`
+ * times (>= 1) with every short length class of the list plan on each of its
+ * two kernels, and keeps per half and class the faster one (CUDA-event time
+ * of its bucket, summed over the runs). Applies the choice to the context and
+ * writes it to *out (may be NULL). ms (may be NULL) receives 16 doubles:
+ * ms[(side * 4 + class) * 2 + kernel], the measured time per run, or -1 for a
+ * class without units. *from_cache (may be NULL) is set to 1 when the choice
+ * came from the cache (ms then holds the stored times).
+ * Cache: cache_path, or when it is NULL the environment variable
+ * NMFKL_TUNE_CACHE, or none; a JSON-lines file, one object per tuned
+ * configuration, keyed by the device name, r, n, m, nnz, each half's unit
+ * count per short length class and each half's density band (tenths) at the
+ * nonzeros; a key found there is applied without measuring, and a new
+ * measurement is appended. Synchronizes. EINVAL without data or with reps < 1. */
+nmfkl_status nmfkl_autotune(nmfkl_ctx *ctx, int64_t sweep, int32_t reps, const char *cache_path,
+                            nmfkl_plan_choice *out, double *ms, int32_t *from_cache);
+
 /* Coordinate orders exactly as the sweep kernels draw them, computed on the
  * device: out[c*r + t] = ids_t of unit cols[c] (device int32 arrays).
  * side 0 = F half, 1 = W half. Synchronizes. */

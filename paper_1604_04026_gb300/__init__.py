@@ -217,6 +217,37 @@ class NMFKL:
                  "list_plan": bool(arr[i].list_plan)}
                 for i in range(min(nb, cap))]
 
+    def plan_choice(self) -> dict:
+        """The launch-plan choices: list_threshold and short_kernel[side][class]."""
+        pc = _native.PlanChoice()
+        self._check(self._lib.nmfkl_get_plan_choice(self._h, ctypes.byref(pc)), "get_plan_choice")
+        return {"list_threshold": pc.list_threshold,
+                "short_kernel": [[int(pc.short_kernel[s][k]) for k in range(4)] for s in range(2)]}
+
+    def set_plan_choice(self, list_threshold=None, short_kernel=None):
+        cur = self.plan_choice()
+        pc = _native.PlanChoice()
+        pc.list_threshold = cur["list_threshold"] if list_threshold is None else float(list_threshold)
+        sk = cur["short_kernel"] if short_kernel is None else short_kernel
+        for s in range(2):
+            for k in range(4):
+                pc.short_kernel[s][k] = int(sk[s][k])
+        self._check(self._lib.nmfkl_set_plan_choice(self._h, ctypes.byref(pc)), "set_plan_choice")
+
+    def autotune(self, sweep: int = 0, reps: int = 1, cache_path: str | None = None) -> dict:
+        """Times both kernels of every short length class of the list plan from
+        the current state (restored afterwards) and applies the faster ones;
+        cached per configuration in cache_path (or NMFKL_TUNE_CACHE)."""
+        pc = _native.PlanChoice()
+        ms = (ctypes.c_double * 16)()
+        fc = ctypes.c_int32()
+        path = cache_path.encode() if cache_path else None
+        self._check(self._lib.nmfkl_autotune(self._h, int(sweep), int(reps), path, ctypes.byref(pc), ms,
+                                             ctypes.byref(fc)), "autotune")
+        return {"short_kernel": [[int(pc.short_kernel[s][k]) for k in range(4)] for s in range(2)],
+                "ms": [[[ms[(s * 4 + k) * 2 + a] for a in range(2)] for k in range(4)] for s in range(2)],
+                "from_cache": bool(fc.value)}
+
     def _get(self, fn, rows, cols, out):
         if out is None:
             out = np.empty((rows, cols), dtype=np.float32)

@@ -33,6 +33,10 @@ class BucketInfo(ctypes.Structure):
                 ("list_plan", c_i32)]
 
 
+class PlanChoice(ctypes.Structure):
+    _fields_ = [("list_threshold", c_f64), ("short_kernel", (c_i32 * 4) * 2)]
+
+
 class ServerCfg(ctypes.Structure):
     _fields_ = [("device", c_i32), ("slots", c_i32), ("mem_budget", c_i64), ("max_pending", c_i32),
                 ("max_batch_docs", c_i32), ("max_batch_nnz", c_i64)]
@@ -69,6 +73,10 @@ SIGNATURES = [
     ("nmfkl_fit", c_i32, [c_vp, c_i64, c_i32, c_f64, c_vp, ctypes.POINTER(c_i32)]),
     ("nmfkl_step", c_i32, [c_vp, c_i64, ctypes.POINTER(c_f64)]),
     ("nmfkl_plan_info", c_i32, [c_vp, c_vp, c_i32]),
+    ("nmfkl_get_plan_choice", c_i32, [c_vp, ctypes.POINTER(PlanChoice)]),
+    ("nmfkl_set_plan_choice", c_i32, [c_vp, ctypes.POINTER(PlanChoice)]),
+    ("nmfkl_autotune", c_i32, [c_vp, c_i64, c_i32, ctypes.c_char_p, ctypes.POINTER(PlanChoice), c_vp,
+                               ctypes.POINTER(c_i32)]),
     ("nmfkl_foldin", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_f64, c_i32, c_vp, c_vp,
                              c_i32, c_i32]),
     ("nmfkl_get_W", c_i32, [c_vp, c_vp, c_i32]),

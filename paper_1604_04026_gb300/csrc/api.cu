@@ -69,6 +69,10 @@ bool dev_alloc(nmfkl_ctx *c, T **p, int64_t count, const char *what) {
 }
 
 void free_data(nmfkl_ctx *c) {
+    if (c->step_graph) {  // the captured step holds the plans' launches
+        cudaGraphExecDestroy(c->step_graph);
+        c->step_graph = nullptr;
+    }
     cudaFree(c->colptr); cudaFree(c->rowptr); cudaFree(c->rowidx); cudaFree(c->colidx);
     cudaFree(c->val); cudaFree(c->rval); cudaFree(c->scratch);
     c->colptr = c->rowptr = nullptr;
@@ -178,15 +182,25 @@ nmfkl_status nmfkl_create(const nmfkl_params *p, int64_t n, int64_t m, int32_t d
     bool ok = dev_alloc(c, &c->Wt, n * c->ldr, "W") && dev_alloc(c, &c->Ft, m * c->ldr, "F") &&
               dev_alloc(c, &c->sumW, c->ldr, "sumW") && dev_alloc(c, &c->sumF, c->ldr, "sumF") &&
               dev_alloc(c, &c->dpart, c->dpart_len, "partials") && dev_alloc(c, &c->dscalar, 8, "scalars") &&
-              dev_alloc(c, &c->counters, 8, "counters") && dev_alloc(c, &c->queues, 64, "queues") &&
+              dev_alloc(c, &c->counters, 8, "counters") && dev_alloc(c, &c->queues, 2 * kQueuesPerSide, "queues") &&
               dev_alloc(c, &c->err_flag, 1, "error flag") && dev_alloc(c, &c->dsum[0], c->ldr, "sumW64") &&
               dev_alloc(c, &c->dsum[1], c->ldr, "sumF64") && dev_alloc(c, &c->unit_obj, n, "row objective") &&
-              dev_alloc(c, &c->dens, 1, "density");
+              dev_alloc(c, &c->dens, 2, "density") && dev_alloc(c, &c->plan_sel, 4, "plan choice") &&
+              dev_alloc(c, &c->dens_out, 2, "density out") && dev_alloc(c, &c->sweep_dev, 1, "sweep index") &&
+              dev_alloc(c, &c->crow_cnt, std::max(n, m), "compressed row counts") &&
+              dev_alloc(c, &c->crow_k, std::max(n, m) * c->ldr, "compressed row indices") &&
+              dev_alloc(c, &c->crow_a, std::max(n, m) * c->ldr, "compressed row values");
+    if (ok && cudaMallocHost((void **)&c->h_sweep, sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_sweep = nullptr;
+        ok = false;
+    }
     if (!ok) {
         nmfkl_destroy(c);
         return NMFKL_ENOMEM;
     }
-    if (!cuda_ok(c, cudaMemset(c->Wt, 0, sizeof(float) * n * c->ldr), "zero W") ||
+    if (!cuda_ok(c, cudaMemset(c->plan_sel, 0, 4 * sizeof(int32_t)), "zero plan choice") ||
+        !cuda_ok(c, cudaMemset(c->Wt, 0, sizeof(float) * n * c->ldr), "zero W") ||
         !cuda_ok(c, cudaMemset(c->Ft, 0, sizeof(float) * m * c->ldr), "zero F") ||
         !cuda_ok(c, cudaMemset(c->counters, 0, sizeof(unsigned long long) * 8), "zero counters") ||
         !cuda_ok(c, cudaMemset(c->err_flag, 0, sizeof(int32_t)), "zero flag")) {
@@ -203,10 +217,15 @@ void nmfkl_destroy(nmfkl_ctx *c) {
     else cudaDeviceSynchronize();
     free_data(c);
     free_fold(c);
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    cudaFree(c->plan_sel); cudaFree(c->dens_out); cudaFree(c->sweep_dev);
+    if (c->h_sweep) cudaFreeHost(c->h_sweep);
     cudaFree(c->Wt); cudaFree(c->Ft); cudaFree(c->sumW); cudaFree(c->sumF); cudaFree(c->dpart);
     cudaFree(c->dscalar); cudaFree(c->counters); cudaFree(c->queues); cudaFree(c->err_flag);
     cudaFree(c->tbuf);
     cudaFree(c->dsum[0]); cudaFree(c->dsum[1]); cudaFree(c->unit_obj); cudaFree(c->dens);
+    cudaFree(c->crow_cnt); cudaFree(c->crow_k); cudaFree(c->crow_a);
     for (auto &pd : c->pending) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -371,10 +390,22 @@ static nmfkl_status clear_flags(nmfkl_ctx *c) {
 // refused.
 static nmfkl_status read_flags(nmfkl_ctx *c) {
     int32_t flag = 0;
+    int32_t sel[2] = {0, 0};
+    double dens[2] = {0.0, 0.0};
     if (!cuda_ok(c, cudaMemcpyAsync(&flag, c->err_flag, sizeof(flag), cudaMemcpyDeviceToHost, c->stream),
                  "copy error flag") ||
+        !cuda_ok(c, cudaMemcpyAsync(sel, c->plan_sel, sizeof(sel), cudaMemcpyDeviceToHost, c->stream),
+                 "copy plan choice") ||
+        !cuda_ok(c, cudaMemcpyAsync(dens, c->dens_out, sizeof(dens), cudaMemcpyDeviceToHost, c->stream),
+                 "copy density") ||
         !cuda_ok(c, cudaStreamSynchronize(c->stream), "error flag sync"))
         return NMFKL_ECUDA;
+    if (c->p.list_mode == 0) {
+        for (int side = 0; side < 2; ++side) {
+            c->used_sparse[side] = sel[side];
+            c->density[side] = dens[side];
+        }
+    }
     if (flag & kErrTimeout) {
         c->err = "a bounded wait on a thread-block cluster peer gave up";
         return NMFKL_ETIMEOUT;
@@ -416,6 +447,86 @@ nmfkl_status nmfkl_objective(nmfkl_ctx *c, double *kl, double *reg) {
     return launch_objective(c, kl, reg);
 }
 
+}  // extern "C"
+
+namespace {
+
+// One pass of the hot path enqueued on the context stream (no host
+// synchronization): the F half, the W half and the fused objective.
+nmfkl_status enqueue_step(nmfkl_ctx *c, int64_t sweep, const int64_t *sweep_dev) {
+    nmfkl_status st = run_half(c, 0, sweep, sweep_dev);
+    if (st == NMFKL_OK) st = run_half(c, 1, sweep, sweep_dev);
+    if (st == NMFKL_OK) st = enqueue_fused_objective(c);
+    return st;
+}
+
+// Captures enqueue_step once into a CUDA graph whose kernels read the sweep
+// index from device memory; rebuilt when the plans change.
+nmfkl_status build_step_graph(nmfkl_ctx *c) {
+    if (!c->cap_stream && !cuda_ok(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking),
+                                   "capture stream"))
+        return NMFKL_ECUDA;
+    cudaStream_t saved = c->stream;
+    const bool saved_timing = c->timing;
+    c->stream = c->cap_stream;
+    c->timing = false;
+    cudaGraph_t g = nullptr;
+    nmfkl_status st = NMFKL_OK;
+    if (!cuda_ok(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture")) {
+        st = NMFKL_ECUDA;
+    } else {
+        st = enqueue_step(c, 0, c->sweep_dev);
+        const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (st == NMFKL_OK && !cuda_ok(c, e, "end capture")) st = NMFKL_ECUDA;
+    }
+    c->stream = saved;
+    c->timing = saved_timing;
+    if (st == NMFKL_OK && !cuda_ok(c, cudaGraphInstantiate(&c->step_graph, g, 0), "instantiate step graph")) {
+        c->step_graph = nullptr;
+        st = NMFKL_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    return st;
+}
+
+// One step: the captured graph (or, with kernel timing on, the same launches
+// issued one by one so that each can be bracketed by events), then the
+// objective, the device flags and the plans chosen, read back in one
+// synchronization. Flags take precedence over a non-finite objective.
+nmfkl_status step_impl(nmfkl_ctx *c, int64_t sweep, double *kl) {
+    nmfkl_status st = clear_flags(c);
+    if (st != NMFKL_OK) return st;
+    if (c->timing) {
+        st = enqueue_step(c, sweep, nullptr);
+    } else {
+        if (!c->step_graph) st = build_step_graph(c);
+        if (st == NMFKL_OK) {
+            *c->h_sweep = sweep;
+            if (!cuda_ok(c, cudaMemcpyAsync(c->sweep_dev, c->h_sweep, sizeof(int64_t), cudaMemcpyHostToDevice,
+                                            c->stream),
+                         "sweep index") ||
+                !cuda_ok(c, cudaGraphLaunch(c->step_graph, c->stream), "step graph launch"))
+                st = NMFKL_ECUDA;
+        }
+    }
+    if (st != NMFKL_OK) return st;
+    double h = 0.0;
+    if (!cuda_ok(c, cudaMemcpyAsync(&h, c->dscalar, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy objective"))
+        return NMFKL_ECUDA;
+    st = read_flags(c);  // synchronizes
+    if (st != NMFKL_OK) return st;
+    if (kl) *kl = h;
+    if (!std::isfinite(h)) {
+        c->err = "objective is not finite";
+        return NMFKL_ENUMERIC;
+    }
+    return NMFKL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 nmfkl_status nmfkl_fit(nmfkl_ctx *c, int64_t sweep0, int32_t max_sweeps, double rel_tol, double *kl_trace,
                        int32_t *sweeps_done) {
     if (!c || max_sweeps < 0 || !(rel_tol >= 0)) return NMFKL_EINVAL;
@@ -425,24 +536,13 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *c, int64_t sweep0, int32_t max_sweeps, double 
     }
     cudaSetDevice(c->device);
     double prev = 0.0;
-    nmfkl_status st = clear_flags(c);
-    if (st == NMFKL_OK) st = launch_objective(c, &prev, nullptr);
+    nmfkl_status st = launch_objective(c, &prev, nullptr);
     if (st != NMFKL_OK) return st;
     int32_t s = 0;
     bool conv = false;
     while (s < max_sweeps) {
-        st = run_half(c, 0, sweep0 + s);
-        if (st == NMFKL_OK) st = run_half(c, 1, sweep0 + s);
         double kl = 0.0;
-        nmfkl_status obj = NMFKL_OK;
-        if (st == NMFKL_OK) obj = launch_fused_objective(c, &kl);
-        // the device flags take precedence over a non-finite objective
-        if (st == NMFKL_OK && (obj == NMFKL_OK || obj == NMFKL_ENUMERIC)) {
-            st = read_flags(c);
-            if (st == NMFKL_OK) st = obj;
-        } else if (st == NMFKL_OK) {
-            st = obj;
-        }
+        st = step_impl(c, sweep0 + s, &kl);
         if (st != NMFKL_OK) {
             if (sweeps_done) *sweeps_done = s;
             return st;
@@ -466,20 +566,16 @@ nmfkl_status nmfkl_step(nmfkl_ctx *c, int64_t sweep, double *kl) {
         return NMFKL_EINVAL;
     }
     cudaSetDevice(c->device);
-    nmfkl_status st = clear_flags(c);
-    if (st == NMFKL_OK) st = run_half(c, 0, sweep);
-    if (st == NMFKL_OK) st = run_half(c, 1, sweep);
-    if (st != NMFKL_OK) return st;
-    const nmfkl_status obj = launch_fused_objective(c, kl);
-    if (obj != NMFKL_OK && obj != NMFKL_ENUMERIC) return obj;
-    // the device flags take precedence over a non-finite objective
-    st = read_flags(c);
-    return st != NMFKL_OK ? st : obj;
+    return step_impl(c, sweep, kl);
 }
 
 nmfkl_status nmfkl_set_wait_limit(nmfkl_ctx *c, int64_t cycles) {
     if (!c || cycles < 0) return NMFKL_EINVAL;
     c->wait_cycles = cycles > 0 ? (long long)cycles : kDefaultWaitCycles;
+    if (c->step_graph) {  // the limit is baked into the captured launches
+        cudaGraphExecDestroy(c->step_graph);
+        c->step_graph = nullptr;
+    }
     return NMFKL_OK;
 }
 
@@ -674,7 +770,10 @@ int32_t nmfkl_plan_info(const nmfkl_ctx *c, nmfkl_bucket_info *out, int32_t cap)
                 out[i].grid = b.grid;
                 out[i].block = b.block;
                 out[i].smem = (int64_t)b.smem;
-                out[i].ran_last = c->used_sparse[side] == lp ? 1 : 0;
+                out[i].ran_last = (c->used_sparse[side] == lp &&
+                                   (b.short_class < 0 || (b.group ? 1 : 0) == c->short_choice[side][b.short_class]))
+                                      ? 1
+                                      : 0;
                 out[i].list_plan = lp;
             }
             ++i;

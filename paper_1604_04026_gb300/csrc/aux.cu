@@ -283,14 +283,19 @@ void launch_colsum_raw(cudaStream_t stream, const float *At, int64_t rows, int l
     colsum_final_kernel<<<1, 256, 0, stream>>>(part, kColsumBlocks, ldr, r, out, out_d);
 }
 
-nmfkl_status launch_fused_objective(nmfkl_ctx *c, double *kl) {
+nmfkl_status enqueue_fused_objective(nmfkl_ctx *c) {
     // sumF (FP64) is current from the W half; sumW changed in it, so sum W again.
     nmfkl_status st = launch_colsum(c, c->Wt, c->n, c->sumW, c->dsum[0]);
     if (st != NMFKL_OK) return st;
     const int tok = timer_begin(c, "objective_fused");
     fused_objective_kernel<<<1, 1024, 0, c->stream>>>(c->unit_obj, c->n, c->dsum[0], c->dsum[1], c->p.r, c->dscalar);
     timer_end(c, tok);
-    if (!cuda_ok(c, cudaGetLastError(), "fused objective")) return NMFKL_ECUDA;
+    return cuda_ok(c, cudaGetLastError(), "fused objective") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
+nmfkl_status launch_fused_objective(nmfkl_ctx *c, double *kl) {
+    nmfkl_status st = enqueue_fused_objective(c);
+    if (st != NMFKL_OK) return st;
     double h = 0.0;
     if (!cuda_ok(c, cudaMemcpyAsync(&h, c->dscalar, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy objective") ||
         !cuda_ok(c, cudaStreamSynchronize(c->stream), "objective sync"))

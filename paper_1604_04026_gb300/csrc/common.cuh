@@ -12,6 +12,7 @@
 namespace nmfkl {
 
 constexpr int kMaxR = 256;
+constexpr int kQueuesPerSide = 64;  // work counters per half (one per bucket of both plans)
 
 // Device error flag bits, set by the kernels and read by the host after a half.
 constexpr int32_t kErrNaN = 1;      // a factor entry came out NaN
@@ -70,6 +71,11 @@ struct HalfArgs {
     const int32_t *idx;   // row of A (= the other factor's row) per nonzero
     const float *val;     // v per nonzero
     const float *At;      // fixed factor, one row of ldr floats per index (W^T or F^T)
+    // the fixed factor's rows compressed to their positive entries, in k order
+    // (row i: ccnt[i] entries at ck/ca[i * ldr ...]); used by the group kernels
+    const int32_t *ccnt;
+    const uint8_t *ck;
+    const float *ca;
     float *X;             // updated factor, one row of ldr floats per unit (F^T or W^T)
     const float *sumA;    // r sums of the fixed factor's columns over its rows
     int32_t r, ldr;
@@ -78,7 +84,13 @@ struct HalfArgs {
     int32_t div_mode;  // 0: IEEE division in the Newton step, 1: fast division
     uint64_t seed;
     int64_t sweep;
+    const int64_t *sweep_dev;  // if set, the sweep index is read here (a captured step replays with new ones)
     int32_t side;
+    // if set, the plan (0: dense tile, 1: lists) the half runs, chosen on the
+    // device from the fixed factor's density; a bucket of the other plan
+    // (plan_id) returns at once
+    const int32_t *plan_sel;
+    int32_t plan_id;
     // bucket
     const int32_t *units;  // unit ids of this bucket, longest first
     int32_t count;
@@ -104,6 +116,7 @@ struct HalfArgs {
 // One launch configuration of the sweep kernel family.
 struct Bucket {
     bool sparse = false;  // kernel table: the sparse-list kinds (else the dense-tile kinds)
+    bool group = false;   // kernel table: the sub-warp group kinds (lists of compressed rows)
     int kind;         // index into the kernel table
     int nt;           // threads per subproblem group (32 = one warp)
     int k;            // nonzeros per thread held in registers (0 = giant)
@@ -119,6 +132,11 @@ struct Bucket {
     int64_t max_len;
     int64_t nnz;      // nonzeros of the bucket's units
     bool borrowed = false;  // a dense bucket reused by the list plan (d_units owned by the dense plan)
+    // list plan, units of at most 256 nonzeros: the length class (0..3 for at
+    // most 32, 64, 128, 256) that this bucket is one alternative for (the
+    // dense-tile warp kernel or the group kernel; the context's choice picks
+    // one per class); -1 for every other bucket
+    int short_class = -1;
 };
 
 // Device state of fold-in (nmfkl_foldin): input copies, per-length-class
@@ -180,7 +198,7 @@ struct nmfkl_ctx {
     int64_t dpart_len = 0;
     double *dscalar = nullptr;     // small FP64 results
     unsigned long long *counters = nullptr;
-    int32_t *queues = nullptr;     // one per bucket per side
+    int32_t *queues = nullptr;     // one per bucket per side (kQueuesPerSide each)
     int32_t *err_flag = nullptr;
     long long wait_cycles = nmfkl::kDefaultWaitCycles;  // bounded device waits
     float *scratch = nullptr;
@@ -190,8 +208,27 @@ struct nmfkl_ctx {
     std::vector<nmfkl::Bucket> plan[2];         // dense-tile kernels
     std::vector<nmfkl::Bucket> plan_sparse[2];  // sparse-list kernels
     unsigned long long *dens = nullptr;         // density numerators of the two halves
+    // device control of a half: [0..1] the plan chosen per half, [2..3] unused,
+    // then two doubles per half (density) and the sweep index (int64)
+    int32_t *plan_sel = nullptr;
+    double *dens_out = nullptr;
+    int64_t *sweep_dev = nullptr;
+    int64_t *h_sweep = nullptr;                 // pinned host copy of the sweep index
+    double list_threshold = 0.5;                // density below which a half runs the list plan
+    // the step (both halves and the objective) captured as one CUDA graph
+    cudaGraphExec_t step_graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    // the fixed factor of the current half compressed to its positive entries
+    // (rows x ldr, rows = max(n, m)); rebuilt at the start of every half
+    int32_t *crow_cnt = nullptr;
+    uint8_t *crow_k = nullptr;
+    float *crow_a = nullptr;
     double density[2] = {-1.0, -1.0};           // last measured density per half
     int used_sparse[2] = {-1, -1};              // which plan the last half ran
+    // list plan: per half and short length class, 0 = dense-tile warp kernel,
+    // 1 = group kernel over the compressed rows (set by nmfkl_set_short_kernels
+    // or the autotuner)
+    int8_t short_choice[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     nmfkl::FoldState *fold = nullptr;
     // timing
     bool timing = false;
@@ -210,19 +247,44 @@ bool cuda_ok(nmfkl_ctx *c, cudaError_t e, const char *what);
 int timer_begin(nmfkl_ctx *c, const char *name);
 void timer_end(nmfkl_ctx *c, int token);
 
+// group.cu: sub-warp group kernels over lists of compressed factor rows
+struct GroupKindInfo {
+    const void *fn;
+    int g;           // lanes per unit
+    int lmax;        // longest unit (nonzeros)
+    const char *name;
+};
+int group_kind_count();
+const GroupKindInfo &group_kind(int kind);
+// Dynamic shared memory of one group and its global scratch slot (floats).
+size_t group_unit_smem(int kind, int r, int ldr);
+size_t group_block_smem(int kind, int r, int ldr, int groups);
+int64_t group_slot_floats(int kind, int r);
+// The default group kind for units of at most L nonzeros (L <= 256), or -1.
+int group_kind_for_length(int64_t L);
+// Compresses the rows of At (rows x ldr) to their positive entries and adds
+// sum_i (wptr[i+1] - wptr[i]) * count_i to *dens (zeroed by the caller).
+void launch_compress(cudaStream_t st, const float *At, int64_t rows, int ldr, int r, const int64_t *wptr,
+                     int32_t *cnt, uint8_t *ck, float *ca, unsigned long long *dens);
+cudaError_t group_attributes(int optin);
+
 // sweep.cu
 // Gives every kernel the device's opt-in dynamic shared memory limit (once per
 // device; the limit is process-wide per-function state).
 cudaError_t kernel_attributes(int device);
 nmfkl_status plan_side(nmfkl_ctx *c, int side);
-nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep);
+nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *sweep_dev = nullptr);
 void free_plan(nmfkl_ctx *c);
 const char *kind_name(int kind);
 const char *bucket_name(const Bucket &b);
+// Kernel timer name of a bucket: "<kernel>/F" or "<kernel>/W" (static storage).
+const char *bucket_timer_name(const Bucket &b, int side);
 
 // aux.cu
 nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out, double *out_d);
 nmfkl_status launch_fused_objective(nmfkl_ctx *c, double *kl);
+// The fused objective's kernels alone (capturable); the value lands in c->dscalar[0].
+nmfkl_status enqueue_fused_objective(nmfkl_ctx *c);
 // colsum into caller buffers: part holds 1024 x ldr doubles.
 void launch_colsum_raw(cudaStream_t stream, const float *At, int64_t rows, int ldr, int r, double *part,
                        float *out, double *out_d);

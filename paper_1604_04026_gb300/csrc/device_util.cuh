@@ -1,0 +1,167 @@
+// Device helpers shared by the sweep kernels of libnmfkl (sweep.cu and
+// group.cu): asynchronous copies, coordinate orders, the x_p step, the
+// projected Newton loop of Algorithm 2 and small reductions.
+#pragma once
+
+#include "common.cuh"
+
+namespace nmfkl {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ constexpr int odd_stride(int r) { return (r & 1) ? r : r + 1; }
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// 4-byte global -> shared copy; src_bytes 0 writes a zero.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+// 16-byte global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Fisher-Yates over {0..r-1} from the identity: step t (i = r-1-t) uses
+// word t, j = floor(word * (i+1) / 2^64).
+__device__ __forceinline__ void fisher_yates(uint8_t *perm, const uint64_t *words, int r) {
+    for (int i = 0; i < r; ++i) perm[i] = (uint8_t)i;
+    int t = 0;
+    for (int i = r - 1; i >= 1; --i, ++t) {
+        const int j = (int)__umul64hi(words[t], (uint64_t)(i + 1));
+        const uint8_t tmp = perm[i];
+        perm[i] = perm[j];
+        perm[j] = tmp;
+    }
+}
+
+// The r-1 Philox words of a unit's order, generated by `nlanes` lanes.
+__device__ __forceinline__ void ids_words_warp(uint64_t *words, int r, int64_t unit, int64_t sweep,
+                                               int side, int perm_mode, uint64_t seed, int lane,
+                                               int nlanes = 32) {
+    const int nw = r - 1;
+    const int nblk = (nw + 3) / 4;
+    for (int b = lane; b < nblk; b += nlanes) {
+        uint64_t c[4];
+        ids_counter(c, (uint64_t)b, unit, sweep, side, perm_mode);
+        philox4x64_10(c, seed, kKeyIds);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (4 * b + j < nw) words[4 * b + j] = c[j];
+    }
+}
+
+// x_p after a step of coordinate k: x_p + d A_pk, where `dc` (+1, -1 or 0)
+// records whether x_k just became positive or just became zero. x_p is a
+// sum of nonnegative terms A_pk x_k; `terms` counts the positive ones. When
+// it reaches 0 the exact value is 0, and any FP32 residual left by the
+// incremental updates is dropped; otherwise the value is kept >= 0.
+__device__ __forceinline__ float step_x(float x, float av, float d, int dc, int &terms) {
+    x = fmaf(d, av, x);
+    if (dc == 0) return fmaxf(x, 0.f);  // no term appears or vanishes (dc is group-uniform)
+    if (av > 0.f) terms += dc;
+    return terms == 0 ? 0.f : fmaxf(x, 0.f);
+}
+
+// 1 / (x + eps) with the hardware approximation (relative error ~1 ulp;
+// x + eps >= eps > 0, so no denormal or zero input).
+__device__ __forceinline__ float recip(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Work counters of one thread (flushed once per kernel; a group processes far
+// fewer than 2^32 coordinates).
+struct Tally {
+    unsigned coords = 0, evals = 0, steps = 0, caps = 0;
+};
+
+__device__ __forceinline__ void flush_tally(const HalfArgs &a, const Tally &t) {
+    if (t.coords) atomicAdd(&a.counters[0], (unsigned long long)t.coords);
+    if (t.evals) atomicAdd(&a.counters[1], (unsigned long long)t.evals);
+    if (t.steps) atomicAdd(&a.counters[2], (unsigned long long)t.steps);
+    if (t.caps) atomicAdd(&a.counters[3], (unsigned long long)t.caps);
+}
+
+// Drops the L2 lines of a finished tile (r rows of `len` floats, row stride
+// lcap) without writing them back: the tile is dead once its unit is done.
+// Whole 128-byte lines only; the partial lines at row ends are left alone.
+__device__ __forceinline__ void discard_tile(float *tile, int r, int len, int lcap, int tid, int nthreads) {
+    const int per_row = (len * 4) / 128;  // full lines from the row start (rows are 128-byte aligned)
+    if (per_row == 0 || (lcap * 4) % 128 != 0) return;
+    const int total = r * per_row;
+    for (int i = tid; i < total; i += nthreads) {
+        const int k = i / per_row, l = i - k * per_row;
+        const char *addr = reinterpret_cast<const char *>(tile + (int64_t)k * lcap) + 128 * l;
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(addr) : "memory");
+    }
+}
+
+// Eq. 1's data term of one nonzero at its final model value (FP32 term).
+__device__ __forceinline__ float kl_term(float v, float x, float eps_div) {
+    return v > 0.f ? v * logf(v / (x + eps_div)) - v : 0.f;
+}
+
+__device__ __forceinline__ double warp_sum_d(double t) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    return t;
+}
+
+// The projected Newton loop of Algorithm 2 for one coordinate. eval() returns
+// (sum_p w_p A_pk, sum_p q_p A_pk^2) over the subproblem; update(d, dc)
+// applies x_p += d A_pk (dc: x_k became positive (+1) or zero (-1)). Every
+// thread of the group runs it with identical values.
+template <class Eval, class Update>
+__device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, float sAk, Eval &&eval,
+                                                   Update &&update, Tally &t) {
+    const float alpha = a.alpha, beta = a.beta;
+    const float tol = a.grad_mode == 0 ? a.eps_grad * (sAk + beta) : a.eps_grad;
+    const float xfloor = a.grad_mode == 0 ? 0.f : a.eps_grad;
+    ++t.coords;
+    // one evaluation site: every pass evaluates, tests, and steps
+    for (int it = 0;; ++it) {
+        const float2 s = eval();
+        ++t.evals;
+        const float g = -s.x + sAk + alpha * xk + beta;
+        const float h = s.y + alpha;
+        if (!(g < -tol || (fabsf(g) > tol && xk > xfloor))) break;
+        if (it == a.max_inner) {
+            ++t.caps;
+            break;
+        }
+        float xn;
+        if (h > 0.f) {
+            xn = xk - (a.div_mode == 0 ? __fdiv_rn(g, h) : __fdividef(g, h));
+            if (xn < 0.f) xn = 0.f;
+        } else {
+            xn = g > 0.f ? 0.f : xk;
+        }
+        const float d = xn - xk;
+        const float xnew = xk + d;
+        const int dc = (xk == 0.f && xnew > 0.f) ? 1 : ((xk > 0.f && xnew == 0.f) ? -1 : 0);
+        if (d != 0.f) update(d, dc);
+        const float xs = xk;
+        xk = xnew;
+        ++t.steps;
+        const bool brk = a.break_mode == 0 ? (fabsf(d) < a.eps_x * xs) : (d < a.eps_x * xs);
+        if (brk) break;
+    }
+    return xk;
+}
+
+// A bucket of the plan the half did not choose returns at once.
+__device__ __forceinline__ bool plan_skip(const HalfArgs &a) { return a.plan_sel && *a.plan_sel != a.plan_id; }
+// The sweep index of the half (from device memory in a captured step).
+__device__ __forceinline__ int64_t sweep_of(const HalfArgs &a) { return a.sweep_dev ? *a.sweep_dev : a.sweep; }
+
+}  // namespace dev
+}  // namespace nmfkl

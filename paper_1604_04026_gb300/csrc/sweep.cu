@@ -17,6 +17,7 @@
 // Reductions are warp xor-butterflies (every lane ends with the same bits),
 // plus for CTA groups one shared-memory exchange per evaluation.
 #include "common.cuh"
+#include "device_util.cuh"
 
 #include <cooperative_groups.h>
 
@@ -28,10 +29,7 @@ namespace nmfkl {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__host__ __device__ constexpr int odd_stride(int r) { return (r & 1) ? r : r + 1; }
-__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+using namespace dev;
 
 // Per-group shared memory: perm (256 B) | x_init, x_out (ldr floats each) |
 // staging rows (8 x odd_stride(r) floats per warp) | CTA partials.
@@ -63,77 +61,12 @@ __host__ __device__ inline RingLayout ring_layout(int r, int ldr, int nt, int k,
     return g;
 }
 
-// 4-byte global -> shared copy; src_bytes 0 writes a zero.
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
-// 16-byte global -> shared copy (both addresses 16-byte aligned).
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Fisher-Yates over {0..r-1} from the identity: step t (i = r-1-t) uses
-// word t, j = floor(word * (i+1) / 2^64).
-__device__ __forceinline__ void fisher_yates(uint8_t *perm, const uint64_t *words, int r) {
-    for (int i = 0; i < r; ++i) perm[i] = (uint8_t)i;
-    int t = 0;
-    for (int i = r - 1; i >= 1; --i, ++t) {
-        const int j = (int)__umul64hi(words[t], (uint64_t)(i + 1));
-        const uint8_t tmp = perm[i];
-        perm[i] = perm[j];
-        perm[j] = tmp;
-    }
-}
-
-// The r-1 Philox words of a unit's order, generated by `nlanes` lanes.
-__device__ __forceinline__ void ids_words_warp(uint64_t *words, int r, int64_t unit, int64_t sweep,
-                                               int side, int perm_mode, uint64_t seed, int lane,
-                                               int nlanes = 32) {
-    const int nw = r - 1;
-    const int nblk = (nw + 3) / 4;
-    for (int b = lane; b < nblk; b += nlanes) {
-        uint64_t c[4];
-        ids_counter(c, (uint64_t)b, unit, sweep, side, perm_mode);
-        philox4x64_10(c, seed, kKeyIds);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (4 * b + j < nw) words[4 * b + j] = c[j];
-    }
-}
-
 // x_p and the number of coordinates with A_pk > 0 and x_k > 0 (the positive
 // terms of x_p) for one staged nonzero.
 struct Staged {
     float x;
     int terms;
 };
-
-// x_p after a step of coordinate k: x_p + d A_pk, where `dc` (+1, -1 or 0)
-// records whether x_k just became positive or just became zero. x_p is a
-// sum of nonnegative terms A_pk x_k; `terms` counts the positive ones. When
-// it reaches 0 the exact value is 0, and any FP32 residual left by the
-// incremental updates is dropped; otherwise the value is kept >= 0.
-__device__ __forceinline__ float step_x(float x, float av, float d, int dc, int &terms) {
-    x = fmaf(d, av, x);
-    if (dc == 0) return fmaxf(x, 0.f);  // no term appears or vanishes (dc is group-uniform)
-    if (av > 0.f) terms += dc;
-    return terms == 0 ? 0.f : fmaxf(x, 0.f);
-}
-
-// 1 / (x + eps) with the hardware approximation (relative error ~1 ulp;
-// x + eps >= eps > 0, so no denormal or zero input).
-__device__ __forceinline__ float recip(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // Stages nonzero p (one per lane; `valid` false for lanes past the unit's
 // end): streams the lane's A row (ldr floats, 16 bytes at a time),
@@ -187,86 +120,6 @@ __device__ __forceinline__ Staged stage_lane(const HalfArgs &a, float *tile, con
     return Staged{acc, cnt};
 }
 
-// Work counters of one thread (flushed once per kernel; a group processes far
-// fewer than 2^32 coordinates).
-struct Tally {
-    unsigned coords = 0, evals = 0, steps = 0, caps = 0;
-};
-
-__device__ __forceinline__ void flush_tally(const HalfArgs &a, const Tally &t) {
-    if (t.coords) atomicAdd(&a.counters[0], (unsigned long long)t.coords);
-    if (t.evals) atomicAdd(&a.counters[1], (unsigned long long)t.evals);
-    if (t.steps) atomicAdd(&a.counters[2], (unsigned long long)t.steps);
-    if (t.caps) atomicAdd(&a.counters[3], (unsigned long long)t.caps);
-}
-
-// Drops the L2 lines of a finished tile (r rows of `len` floats, row stride
-// lcap) without writing them back: the tile is dead once its unit is done.
-// Whole 128-byte lines only; the partial lines at row ends are left alone.
-__device__ __forceinline__ void discard_tile(float *tile, int r, int len, int lcap, int tid, int nthreads) {
-    const int per_row = (len * 4) / 128;  // full lines from the row start (rows are 128-byte aligned)
-    if (per_row == 0 || (lcap * 4) % 128 != 0) return;
-    const int total = r * per_row;
-    for (int i = tid; i < total; i += nthreads) {
-        const int k = i / per_row, l = i - k * per_row;
-        const char *addr = reinterpret_cast<const char *>(tile + (int64_t)k * lcap) + 128 * l;
-        asm volatile("discard.global.L2 [%0], 128;" ::"l"(addr) : "memory");
-    }
-}
-
-// Eq. 1's data term of one nonzero at its final model value (FP32 term).
-__device__ __forceinline__ float kl_term(float v, float x, float eps_div) {
-    return v > 0.f ? v * logf(v / (x + eps_div)) - v : 0.f;
-}
-
-__device__ __forceinline__ double warp_sum_d(double t) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-    return t;
-}
-
-// The projected Newton loop of Algorithm 2 for one coordinate. eval() returns
-// (sum_p w_p A_pk, sum_p q_p A_pk^2) over the subproblem; update(d, dc)
-// applies x_p += d A_pk (dc: x_k became positive (+1) or zero (-1)). Every
-// thread of the group runs it with identical values.
-template <class Eval, class Update>
-__device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, float sAk, Eval &&eval,
-                                                   Update &&update, Tally &t) {
-    const float alpha = a.alpha, beta = a.beta;
-    const float tol = a.grad_mode == 0 ? a.eps_grad * (sAk + beta) : a.eps_grad;
-    const float xfloor = a.grad_mode == 0 ? 0.f : a.eps_grad;
-    ++t.coords;
-    // one evaluation site: every pass evaluates, tests, and steps
-    for (int it = 0;; ++it) {
-        const float2 s = eval();
-        ++t.evals;
-        const float g = -s.x + sAk + alpha * xk + beta;
-        const float h = s.y + alpha;
-        if (!(g < -tol || (fabsf(g) > tol && xk > xfloor))) break;
-        if (it == a.max_inner) {
-            ++t.caps;
-            break;
-        }
-        float xn;
-        if (h > 0.f) {
-            xn = xk - (a.div_mode == 0 ? __fdiv_rn(g, h) : __fdividef(g, h));
-            if (xn < 0.f) xn = 0.f;
-        } else {
-            xn = g > 0.f ? 0.f : xk;
-        }
-        const float d = xn - xk;
-        const float xnew = xk + d;
-        const int dc = (xk == 0.f && xnew > 0.f) ? 1 : ((xk > 0.f && xnew == 0.f) ? -1 : 0);
-        if (d != 0.f) update(d, dc);
-        const float xs = xk;
-        xk = xnew;
-        ++t.steps;
-        const bool brk = a.break_mode == 0 ? (fabsf(d) < a.eps_x * xs) : (d < a.eps_x * xs);
-        if (brk) break;
-    }
-    return xk;
-}
-
 // ---------------------------------------------------------------------------
 // Register-resident groups: NT threads (32 = one warp per subproblem, several
 // per block; otherwise one CTA), K nonzeros per thread, so L <= NT*K.
@@ -287,6 +140,7 @@ constexpr int kModeHalf = 0, kModeFree = 1, kModeFold = 2;
 
 template <int NT, int K, int D, int kMode = kModeHalf>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) sweep_kernel(HalfArgs a) {
+    if (plan_skip(a)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
     constexpr int kNW = NT / 32;
@@ -552,7 +406,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                 a.unit_final[u] = prev;
             }
         } else {
-            run_coordinates(a.sweep);
+            run_coordinates(sweep_of(a));
             if (a.unit_obj) {
                 float t = 0.f;
 #pragma unroll
@@ -581,6 +435,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
 constexpr int kGiantNT = 512;
 
 __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
+    if (plan_skip(a)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kNW = kGiantNT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -640,7 +495,7 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
             }
         }
         if (warp == 0) {
-            ids_words_warp(words, r, u, a.sweep, a.side, a.perm_mode, a.seed, lane);
+            ids_words_warp(words, r, u, sweep_of(a), a.side, a.perm_mode, a.seed, lane);
             __syncwarp();
             if (lane == 0) fisher_yates(perm, words, r);
             __syncwarp();
@@ -770,6 +625,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
 
 template <int NT, int K, int D>
 __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
+    if (plan_skip(a)) return;  // uniform over the cluster: every CTA reads the same selection
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const uint32_t crank = cluster.block_rank();
@@ -888,7 +744,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
             }
         }
         if (warp == 0) {
-            ids_words_warp(words, r, u, a.sweep, a.side, a.perm_mode, a.seed, lane);
+            ids_words_warp(words, r, u, sweep_of(a), a.side, a.perm_mode, a.seed, lane);
             __syncwarp();
             if (lane == 0) fisher_yates(perm, words, r);
             __syncwarp();
@@ -1087,6 +943,7 @@ __host__ __device__ constexpr int sparse_min_blocks() {
 // CTAs.) Clusters take units from the bucket's queue, longest first.
 template <int NT, bool kSmemState, bool kCompact = false, bool kCluster = false>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kSmemState>())) sparse_kernel(HalfArgs a) {
+    if (plan_skip(a)) return;  // uniform over a cluster: every CTA reads the same selection
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
     // lanes per warp-level group: the whole warp (groups of 8 or 16 lanes,
@@ -1366,7 +1223,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             __syncwarp(gmask);
         }
         if (w == 0) {
-            ids_words_warp(words, r, perm_unit, a.sweep, a.side, a.perm_mode, a.seed, glane, CH);
+            ids_words_warp(words, r, perm_unit, sweep_of(a), a.side, a.perm_mode, a.seed, glane, CH);
             __syncwarp(gmask);
             if (glane == 0) fisher_yates(perm, words, r);
             __syncwarp(gmask);
@@ -1777,7 +1634,10 @@ int sparse_kind_for_length(int64_t L, int r, int ldr, int optin, const std::vect
 }  // namespace
 
 const char *kind_name(int kind) { return kKinds[kind].name; }
-const char *bucket_name(const Bucket &b) { return b.sparse ? kSparseKinds[b.kind].name : kKinds[b.kind].name; }
+const char *bucket_name(const Bucket &b) {
+    if (b.group) return group_kind(b.kind).name;
+    return b.sparse ? kSparseKinds[b.kind].name : kKinds[b.kind].name;
+}
 
 // Kernel timer name of a bucket: "<kernel>/F" or "<kernel>/W" (static storage).
 const char *bucket_timer_name(const Bucket &b, int side) {
@@ -1786,11 +1646,13 @@ const char *bucket_timer_name(const Bucket &b, int side) {
         for (int s = 0; s < 2; ++s) {
             for (int i = 0; i < kNumKinds; ++i) v.push_back(std::string(kKinds[i].name) + (s ? "/W" : "/F"));
             for (int i = 0; i < kNumSparseKinds; ++i) v.push_back(std::string(kSparseKinds[i].name) + (s ? "/W" : "/F"));
+            for (int i = 0; i < group_kind_count(); ++i) v.push_back(std::string(group_kind(i).name) + (s ? "/W" : "/F"));
         }
         return v;
     }();
-    const int per = kNumKinds + kNumSparseKinds;
-    return names[side * per + (b.sparse ? kNumKinds + b.kind : b.kind)].c_str();
+    const int per = kNumKinds + kNumSparseKinds + group_kind_count();
+    const int idx = b.group ? kNumKinds + kNumSparseKinds + b.kind : (b.sparse ? kNumKinds + b.kind : b.kind);
+    return names[side * per + idx].c_str();
 }
 
 
@@ -1828,12 +1690,14 @@ std::vector<int32_t> order_by_length(const std::vector<int64_t> &ptr) {
     return order;
 }
 
-// Units of at most this many nonzeros keep the dense tile in the list plan:
-// their coordinate loop is bound by the fixed latency of each evaluation, and
-// the tile ring prefetches several coordinates ahead where the lists fetch
-// one. Measured on the large corpus at r = 100 (ms per step): 117.1 with no
-// dense units in the list plan, 110.2 up to 128, 109.4 up to 256, 115.5 up to
-// 512.
+// Units of at most this many nonzeros have two alternatives in the list plan,
+// chosen per length class (at most 32, 64, 128, 256 nonzeros): the dense-tile
+// warp kernels of the dense plan, or the sub-warp group kernels over lists of
+// the compressed factor rows. Measured on the large corpus at r = 100 at a
+// steady state (sweep 9, the fixed factor ~13% dense at the nonzeros), ms per
+// F half: dense 2.39 / 4.54 / 7.91 / 10.90, group 2.16 / 6.80 / 12.0 / 16.4
+// (the group kernels' list building, about half their time, issues one
+// scattered store per list entry); the dense kernels are the default.
 constexpr int64_t kDenseBelow = 256;
 
 // Sparse-list plan of one half: the dense buckets of the units of at most
@@ -1853,12 +1717,71 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
         clusters_fit[i] = sparse_active_clusters(kSparseKinds[i], (size_t)optin);
         usable[i] = clusters_fit[i] > 0;
     }
+    // units of at most kDenseBelow nonzeros: the dense-tile warp buckets of the
+    // dense plan, and the group kinds, by length (one alternative per class runs)
     for (const Bucket &d : c->plan[side]) {
         const KernelKind &kk = kKinds[d.kind];
-        if (kk.cl == 1 && kk.k > 0 && (int64_t)kk.nt * kk.k <= kDenseBelow) {
+        if (kk.cl == 1 && kk.k > 0 && kk.nt == 32 && (int64_t)kk.nt * kk.k <= kDenseBelow) {
             Bucket b = d;
             b.borrowed = true;
+            b.short_class = group_kind_for_length((int64_t)kk.nt * kk.k);
             c->plan_sparse[side].push_back(b);
+        }
+    }
+    {
+        const int ngk = group_kind_count();
+        std::vector<std::vector<int32_t>> glists(ngk);
+        std::vector<int64_t> gmax(ngk, 0), gnnz(ngk, 0);
+        for (int32_t u : order) {
+            const int64_t L = ptr[u + 1] - ptr[u];
+            if (L > kDenseBelow) continue;
+            const int gk = group_kind_for_length(L);
+            glists[gk].push_back(u);
+            gmax[gk] = std::max(gmax[gk], L);
+            gnnz[gk] += L;
+        }
+        for (int gk = 0; gk < ngk; ++gk) {
+            if (glists[gk].empty()) continue;
+            const GroupKindInfo &info = group_kind(gk);
+            Bucket b{};
+            b.sparse = true;
+            b.group = true;
+            b.kind = gk;
+            b.nt = info.g;
+            b.k = 0;
+            b.cl = 1;
+            b.count = (int32_t)glists[gk].size();
+            b.max_len = gmax[gk];
+            b.nnz = gnnz[gk];
+            b.lcap = info.lmax;
+            b.short_class = gk;
+            b.block = 256;
+            const int gpb = b.block / info.g;
+            b.smem = group_block_smem(gk, r, ldr, gpb);
+            if (b.smem > (size_t)optin) {
+                c->err = "group plan: shared memory exceeds the device limit";
+                return NMFKL_EINVAL;
+            }
+            int per_sm = 0;
+            if (!cuda_ok(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, info.fn, b.block, b.smem),
+                         "occupancy"))
+                return NMFKL_ECUDA;
+            if (per_sm < 1) {
+                c->err = std::string("kernel ") + info.name + " cannot be resident";
+                return NMFKL_EINVAL;
+            }
+            const int64_t need_blocks = (b.count + gpb - 1) / gpb;
+            b.grid = (int)std::min<int64_t>(need_blocks, (int64_t)per_sm * c->num_sms);
+            b.groups = b.grid * gpb;
+            b.slot_floats = group_slot_floats(gk, r);
+            if (!cuda_ok(c, cudaMalloc(&b.d_units, sizeof(int32_t) * glists[gk].size()), "alloc unit list"))
+                return NMFKL_ENOMEM;
+            if (!cuda_ok(c, cudaMemcpy(b.d_units, glists[gk].data(), sizeof(int32_t) * glists[gk].size(),
+                                       cudaMemcpyHostToDevice),
+                         "copy unit list"))
+                return NMFKL_ECUDA;
+            c->plan_sparse[side].push_back(b);
+            c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
         }
     }
     // in decreasing length, so each class's list comes out longest first; the
@@ -2050,7 +1973,49 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
     return plan_side_sparse(c, side, ptr, order, optin);
 }
 
-nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
+namespace {
+// Launches one bucket of a half on stream st.
+cudaError_t launch_bucket(const Bucket &b, HalfArgs &a, cudaStream_t st) {
+    void *args[] = {&a};
+    if (b.group) return cudaLaunchKernel(group_kind(b.kind).fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
+    if (b.sparse && b.cl == 1)
+        return cudaLaunchKernel(kSparseKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
+    if (b.cl > 1) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(b.grid);
+        cfg.blockDim = dim3(b.block);
+        cfg.dynamicSmemBytes = b.smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = b.cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelExC(&cfg, b.sparse ? kSparseKinds[b.kind].fn : kKinds[b.kind].fn, args);
+    }
+    return cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
+}
+
+// The plan of a half from the fixed factor's density at the nonzeros of V
+// (sum of row counts weighted by row lengths, over nnz * r): the lists below
+// the threshold, else the dense tile.
+__global__ void plan_select_kernel(const unsigned long long *dens, double denom, double threshold, int32_t *sel,
+                                   double *dens_out) {
+    const double d = denom > 0.0 ? (double)*dens / denom : 0.0;
+    *dens_out = d;
+    *sel = d < threshold ? 1 : 0;
+}
+}  // namespace
+
+// One half of Algorithm 1 on the context stream, without any host
+// synchronization (capturable): sumA, the compressed rows of the fixed
+// factor and their density, the device-side choice of plan (list_mode 0),
+// then every bucket of the plans that may run, in order; a bucket of the plan
+// not chosen returns at once. With `sweep_dev` set the kernels read the sweep
+// index from it (a captured step), else they take `sweep`.
+nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *sweep_dev) {
     const bool F = side == 0;
     const float *At = F ? c->Wt : c->Ft;
     float *X = F ? c->Ft : c->Wt;
@@ -2078,67 +2043,64 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep) {
     a.perm_mode = c->p.perm_mode;
     a.seed = c->p.seed;
     a.sweep = sweep;
+    a.sweep_dev = sweep_dev;
     a.side = side;
     a.scratch = c->scratch;
     a.counters = c->counters;
     a.err = c->err_flag;
     a.wait_cycles = c->wait_cycles;
     a.unit_obj = F ? nullptr : c->unit_obj;
-    // dense tile or sparse lists (list_mode): in automatic mode, the lists when
-    // the fixed factor is less than half dense at the nonzeros of V
-    bool sparse = c->p.list_mode == 2;
-    if (c->p.list_mode == 0) {
-        unsigned long long h = 0;
-        if (!cuda_ok(c, cudaMemsetAsync(c->dens, 0, sizeof(unsigned long long), c->stream), "density reset"))
-            return NMFKL_ECUDA;
-        launch_density(c->stream, At, F ? c->n : c->m, c->ldr, c->p.r, F ? c->rowptr : c->colptr, c->dens);
-        if (!cuda_ok(c, cudaMemcpyAsync(&h, c->dens, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "density") ||
-            !cuda_ok(c, cudaStreamSynchronize(c->stream), "density sync"))
-            return NMFKL_ECUDA;
-        c->density[side] = c->nnz > 0 ? (double)h / ((double)c->nnz * c->p.r) : 0.0;
-        sparse = c->density[side] < 0.5;
+    a.ccnt = c->crow_cnt;
+    a.ck = c->crow_k;
+    a.ca = c->crow_a;
+    // The fixed factor's rows compressed to their positive entries (for the
+    // group kernels of the list plan); the same pass measures the factor's
+    // density at the nonzeros of V.
+    if (!cuda_ok(c, cudaMemsetAsync(c->dens + side, 0, sizeof(unsigned long long), c->stream), "density reset"))
+        return NMFKL_ECUDA;
+    {
+        const int tok = timer_begin(c, "compress_rows");
+        launch_compress(c->stream, At, F ? c->n : c->m, c->ldr, c->p.r, F ? c->rowptr : c->colptr, c->crow_cnt,
+                        c->crow_k, c->crow_a, c->dens + side);
+        timer_end(c, tok);
+        if (!cuda_ok(c, cudaGetLastError(), "compress rows")) return NMFKL_ECUDA;
     }
-    c->used_sparse[side] = sparse ? 1 : 0;
+    // dense tile or sparse lists (list_mode): in automatic mode, chosen on the
+    // device, the lists when the fixed factor is less dense than the threshold
+    // at the nonzeros of V; 1 and 2 fix the plan
+    bool run_plan[2] = {c->p.list_mode != 2, c->p.list_mode != 1};
+    if (c->p.list_mode == 0) {
+        const double denom = (double)c->nnz * c->p.r;
+        plan_select_kernel<<<1, 1, 0, c->stream>>>(c->dens + side, denom, c->list_threshold, c->plan_sel + side,
+                                                    c->dens_out + side);
+        if (!cuda_ok(c, cudaGetLastError(), "plan select")) return NMFKL_ECUDA;
+        a.plan_sel = c->plan_sel + side;
+    } else {
+        c->used_sparse[side] = c->p.list_mode == 2 ? 1 : 0;
+    }
     // Buckets run one after another on the context stream. (Running them
     // concurrently on side streams, so that one bucket's tail overlaps the
     // next one's work, was measured slower: 139 vs 133 ms per step on the
     // large corpus; the concurrent persistent kernels contend for L2.)
-    std::vector<Bucket> &plan = sparse ? c->plan_sparse[side] : c->plan[side];
     int qi = 0;
-    for (auto &b : plan) {
-        cudaStream_t st = c->stream;
-        a.units = b.d_units;
-        a.count = b.count;
-        a.queue = c->queues + side * 16 + qi++;
-        a.slot_floats = b.slot_floats;
-        a.lcap = b.lcap;
-        a.scratch = c->scratch;
-        if (!cuda_ok(c, cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st), "reset queue"))
-            return NMFKL_ECUDA;
-        void *args[] = {&a};
-        const int tok = timer_begin(c, bucket_timer_name(b, side));
-        cudaError_t e;
-        if (b.sparse && b.cl == 1) {
-            e = cudaLaunchKernel(kSparseKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
-        } else if (b.cl > 1) {
-            cudaLaunchConfig_t cfg{};
-            cfg.gridDim = dim3(b.grid);
-            cfg.blockDim = dim3(b.block);
-            cfg.dynamicSmemBytes = b.smem;
-            cfg.stream = st;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = b.cl;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            e = cudaLaunchKernelExC(&cfg, b.sparse ? kSparseKinds[b.kind].fn : kKinds[b.kind].fn, args);
-        } else {
-            e = cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
+    for (int lp = 0; lp < 2; ++lp) {
+        if (!run_plan[lp]) continue;
+        a.plan_id = lp;
+        for (auto &b : lp ? c->plan_sparse[side] : c->plan[side]) {
+            // the alternative of a short length class that was not chosen
+            if (b.short_class >= 0 && (b.group ? 1 : 0) != c->short_choice[side][b.short_class]) continue;
+            a.units = b.d_units;
+            a.count = b.count;
+            a.queue = c->queues + side * kQueuesPerSide + qi++;
+            a.slot_floats = b.slot_floats;
+            a.lcap = b.lcap;
+            if (!cuda_ok(c, cudaMemsetAsync(a.queue, 0, sizeof(int32_t), c->stream), "reset queue"))
+                return NMFKL_ECUDA;
+            const int tok = timer_begin(c, bucket_timer_name(b, side));
+            const cudaError_t e = launch_bucket(b, a, c->stream);
+            timer_end(c, tok);
+            if (!cuda_ok(c, e, bucket_name(b))) return NMFKL_ECUDA;
         }
-        timer_end(c, tok);
-        if (!cuda_ok(c, e, bucket_name(b))) return NMFKL_ECUDA;
     }
     return NMFKL_OK;
 }
@@ -2601,6 +2563,7 @@ cudaError_t kernel_attributes(int device) {
             if (e != cudaSuccess) break;
             e = set_attrs_for(kk.fn, optin);
         }
+        if (e == cudaSuccess) e = group_attributes(optin);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kKinds[kGiantKind - 1].fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         for (int i = 0; e == cudaSuccess && i < kNumSparseKinds; ++i)

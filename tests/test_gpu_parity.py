@@ -118,15 +118,19 @@ def test_objective_matches_oracle(which, docs_small):
 OBJ_REL = 2e-6
 
 
-def _halves(V, W0, F0, p, threads=8):
+def _halves(V, W0, F0, p, threads=8, short_kernel=None):
     cF, cW = cfg_for(p, 0), cfg_for(p, 1)
     m = model(V, W0, F0, p)
+    if short_kernel is not None:
+        m.set_plan_choice(short_kernel=short_kernel)
     m.sweep_F(0)
     Fg = m.get_F()
     m.close()
     Fo, _ = oracle.half_F(V, W0, F0, p.seed, 0, cF, threads=threads)
     F1 = Fo.astype(np.float32)
     m = model(V, W0, F1, p)
+    if short_kernel is not None:
+        m.set_plan_choice(short_kernel=short_kernel)
     m.sweep_W(0)
     Wg = m.get_W()
     m.close()
@@ -156,18 +160,18 @@ def _check_halves(V, W0, F0, Fg, Fo, Wg, Wo, F1, p, fraction=None, obj_rel=OBJ_R
 
 def test_designed_lengths_reach_every_list_class(designed):
     """The designed lengths put units into every reachable class of the list
-    plan on both halves: the dense-tile warp buckets it keeps for units of at
-    most 256 nonzeros, then the list classes (the tight parity test above
-    then covers each of them)."""
+    plan on both halves: the sub-warp group kernels for units of at most 256
+    nonzeros, then the list classes (the tight parity test above then covers
+    each of them)."""
     r = 16
     W0, F0 = start(designed, r, seed=2)
     m = model(designed, W0, F0, params(r, seed=5, list_mode=2))
-    want = {"sweep_warp_k1", "sweep_warp_k2", "sweep_warp_k4", "sweep_warp_k8", "sparse_warp", "sparse_warp_1k",
+    want = {"group_g4_l32", "group_g8_l64", "group_g8_l128", "group_g16_l256", "sparse_warp", "sparse_warp_1k",
             "sparse_cta128", "sparse_cta256", "sparse_cta512", "sparse_cluster2"}
     for side in (0, 1):
         kinds = {b["kernel"] for b in m.plan() if b["side"] == side and b["list_plan"]}
         assert want <= kinds, (side, want - kinds)
-        assert not kinds & {"sweep_warp_k16", "sweep_cta128_k8"}, kinds
+        assert not kinds & {"sweep_warp_k1", "sweep_warp_k8", "sweep_warp_k16", "sweep_cta128_k8"}, kinds
     m.close()
 
 
@@ -182,6 +186,22 @@ def test_halves_tight_every_bucket(designed, list_mode):
     W0, F0 = start(V, r, seed=2)
     p = params(r, seed=5, list_mode=list_mode, **TIGHT)
     _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, name="tight_every_bucket/lm%d" % list_mode)
+
+
+@pytest.mark.parametrize("case", ["designed", "docs_r37", "reg"])
+def test_halves_tight_group_kernels(case, designed, docs_small):
+    """The sub-warp group kernels (list plan, units of at most 256 nonzeros,
+    chosen for every class) under the tight-mode bar."""
+    if case == "designed":
+        V, r, extra = designed, 16, {}
+    elif case == "docs_r37":
+        V, r, extra = docs_small, 37, {}
+    else:
+        V, r, extra = docs_small, 12, dict(alpha_W=0.5, beta_W=0.1, alpha_F=0.2, beta_F=0.3)
+    W0, F0 = start(V, r, seed=7)
+    p = params(r, seed=11, list_mode=2, **TIGHT, **extra)
+    _check_halves(V, W0, F0, *_halves(V, W0, F0, p, short_kernel=[[1] * 4, [1] * 4]), p,
+                  name="tight_group_%s" % case)
 
 
 @pytest.mark.parametrize("list_mode", LIST_MODES)
