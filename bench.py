@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-target and fold-in legs of the default line")
     ap.add_argument("--threads", type=int, default=0, help="host threads (0 = all cores)")
     ap.add_argument("--sample-div", type=int, default=16,
                     help="CPU legs run on the first m/sample_div documents")
@@ -290,10 +292,14 @@ def run_ours(args):
         sweep += 1
     model.counters(reset=True)
     model.kernel_times(reset=True)
-    # per-kernel CUDA events on the library's stream (the buckets run one after
-    # another there anyway) give the breakdown and the launch count of the
-    # timed steps
-    model.set_timing(True)
+    # the launch plan's autotuner, from the state the timed steps start from
+    # (which it leaves unchanged); cached per configuration in NMFKL_TUNE_CACHE
+    # when that is set
+    tune = model.autotune(sweep=sweep, reps=1)
+    hand_picked = [[0] * 4, [0] * 4]
+    # the state the timed steps start from: the per-kernel breakdown replays
+    # the same sweeps from it afterwards
+    state0, sweep0 = model.get_state(sweep), sweep
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -313,9 +319,54 @@ def run_ours(args):
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
     counters = model.counters(reset=True)
+    plan_all = model.plan()  # both plans (dense tile, sparse lists) of both halves
+    # The timed steps replay the captured step graph. The breakdown and the
+    # launch count come from the same sweeps replayed from the same state with
+    # per-kernel CUDA events on the library's stream, which issues the same
+    # launches one by one (the results are bit-identical, tested).
+    model.set_state(state0)
+    model.set_timing(True)
+    for s in range(sweep0, sweep0 + args.steps):
+        model.step(s)
     model.set_timing(False)
     times = model.kernel_times(reset=True)
-    plan_all = model.plan()  # both plans (dense tile, sparse lists) of both halves
+    # Table 2 analogue: exact zeros of W and F after the timed sweeps
+    W_end, F_end = model.get_W(), model.get_F()
+    zeros = {"W_pct": 100.0 * float((W_end == 0).mean()), "F_pct": 100.0 * float((F_end == 0).mean()),
+             "after_sweeps": sweep0 + args.steps}
+    del W_end, F_end
+    # the hand-picked plan on the same sweeps, when the tuner chose otherwise
+    plan_leg = {"tuned_short_kernel": tune["short_kernel"], "from_cache": tune["from_cache"],
+                "tuning_ms_per_half_class_kernel": tune["ms"], "hand_picked_short_kernel": hand_picked,
+                "ms_per_step_tuned": ms / args.steps, "ms_per_step_hand_picked": None}
+    if tune["short_kernel"] != hand_picked:
+        model.set_state(state0)
+        model.set_plan_choice(short_kernel=hand_picked)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(sweep0, sweep0 + args.steps):
+            model.step(s)
+        e1.record()
+        barrier()
+        plan_leg["ms_per_step_hand_picked"] = e0.elapsed_time(e1) / args.steps
+        model.set_plan_choice(short_kernel=tune["short_kernel"])
+    else:
+        plan_leg["ms_per_step_hand_picked"] = plan_leg["ms_per_step_tuned"]
+    # time to the KL target from the seeded start (Algorithm 1 until the
+    # objective changes by at most kl_rel_tol in one sweep), same resident data
+    time_to_kl = None
+    if rank == 0 and not args.no_extras:
+        model.init()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        trace, done = model.fit(args.max_sweeps, rel_tol=args.kl_rel_tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        time_to_kl = {"value": dt, "unit": "s", "sweeps": int(done), "converged": bool(done < args.max_sweeps),
+                      "kl_final": float(trace[-1]) if done else None,
+                      "target": "relative KL change per sweep <= %g from the seeded Uniform[0,1) start"
+                                % args.kl_rel_tol}
     value = ws * U * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel (timers are per kernel and half,
@@ -358,6 +409,16 @@ def run_ours(args):
         cpu = {"value": 2 * Vs.nnz * r / t, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "one FP64 oracle sweep on the first %d of %d documents (%d nnz)" % (Vs.m, V.m, Vs.nnz),
                "seconds": t, "cpu": cpu_desc()}
+        # the paper's own setting runs one CPU thread (Section 4)
+        Vs1 = subsample(V, args.sample_div * 16)
+        t1 = oracle_sweep_time(Vs1, r, args.seed, 1, 1)
+        cpu["single_thread"] = {"value": 2 * Vs1.nnz * r / t1, "unit": UNIT, "cores": 1,
+                                "sample": "one FP64 oracle sweep, one thread, on the first %d of %d documents "
+                                          "(%d nnz)" % (Vs1.m, V.m, Vs1.nnz), "seconds": t1}
+
+    foldin = None
+    if rank == 0 and not args.no_extras:
+        foldin = foldin_measure(args, nk, torch, local, steps=5, warmup=2)
 
     if rank == 0:
         line = {
@@ -373,6 +434,10 @@ def run_ours(args):
             "clocks": clocks.summary(),
             "gpu_launches": n_launch,
             "kl_after": kl,
+            "time_to_kl": time_to_kl,
+            "foldin": foldin,
+            "zeros": zeros,
+            "plan": plan_leg,
             "counters": counters,
             "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(times.items())},
         }
@@ -460,18 +525,13 @@ def run_fit(args):
 
 
 # --------------------------------------------------------------------------- fold-in
-def run_foldin(args):
+def foldin_measure(args, nk, torch, local, steps, warmup):
     """Batched fold-in of new documents under a fixed W: one launch sequence per
     batch captured in a CUDA graph, against the plain scheme of one launch per
-    document on the same inputs (identical results, checked)."""
-    import torch
-    import paper_1604_04026_gb300 as nk
+    document on the same inputs (identical results, checked). Returns the
+    measurements as a dict."""
     from paper_1604_04026_gb300 import synth
 
-    ws, rank, local = dist_env()
-    if ws > 1 and rank != 0:
-        return 0
-    torch.cuda.set_device(local)
     threads = args.threads or os.cpu_count() or 1
     n, K = 30_000, args.r
     topics, V = synth.foldin_docs(n, args.docs, K, seed=args.seed, threads=threads)
@@ -494,39 +554,39 @@ def run_foldin(args):
         return model.foldin(colptr=d["colptr"], rowidx=d["rowidx"], val=d["val"], F0=F0, rel_tol=1e-5,
                             max_sweeps=200, launch_mode=mode)
 
-    def timed(mode, steps, warm):
+    def timed(mode, k, warm):
         for _ in range(warm):
             out = run(mode)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        for _ in range(steps):
+        for _ in range(k):
             out = run(mode)
         ev1.record()
         torch.cuda.synchronize()
-        return ev0.elapsed_time(ev1) / steps, out
+        return ev0.elapsed_time(ev1) / k, out
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms_graph, out_g = timed(0, args.steps, args.warmup)
+    ms_graph, out_g = timed(0, steps, warmup)
     clocks.stop()
-    ms_plain, out_p = timed(1, args.steps, 1)
+    ms_plain, out_p = timed(1, steps, 1)
     ms_doc, out_d = timed(2, 1, 1)
     same = all(torch.equal(a, b) for a, b in zip(out_g, out_p)) and \
         torch.equal(out_g[0][:, :sample], out_d[0]) and torch.equal(out_g[1][:sample], out_d[1]) and \
         torch.equal(out_g[2][:sample], out_d[2])
     sweeps = out_g[1].double()
     # end to end: host inputs and outputs through the public call
+    F0h = F0.cpu().numpy()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        Fh, sh, oh = model.foldin(V, F0=F0.cpu().numpy(), rel_tol=1e-5, max_sweeps=200)
-    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    for _ in range(steps):
+        model.foldin(V, F0=F0h, rel_tol=1e-5, max_sweeps=200)
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / steps
     h2d = V.colptr.nbytes + V.rowidx.nbytes + V.val.nbytes + 4 * K * V.m
     d2h = 4 * K * V.m + 4 * V.m + 8 * V.m
-    line = {
-        "metric": "fold-in batch latency", "value": ms_graph, "unit": "ms", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    model.close()
+    return {
+        "metric": "fold-in batch latency", "value": ms_graph, "unit": "ms", "steps": steps, "warmup": warmup,
         "config": {"workload": "batched fold-in: fixed W = the generator's %d topic-word laws over n=%d words, "
                                "%d new documents, Pareto(5, 1.5) distinct words capped at 5000" % (K, n, V.m),
                    "nnz": V.nnz, "rel_tol": 1e-5, "l2": "inputs smaller than L2; no flush between batches"},
@@ -538,8 +598,22 @@ def run_foldin(args):
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks.summary(),
     }
+
+
+def run_foldin(args):
+    """The fold-in leg alone, as its own JSON line."""
+    import torch
+    import paper_1604_04026_gb300 as nk
+
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    res = foldin_measure(args, nk, torch, local, args.steps, args.warmup)
+    line = dict(res)
+    line.update({"n_gpus": 1, "ms_per_step": res["value"], "higher_is_better": False, "scaling": "weak",
+                 "vs_baseline": None, "dtype": "f32", "data": "synthetic"})
     print(json.dumps(line), flush=True)
-    model.close()
     return 0
 
 
