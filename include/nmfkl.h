@@ -147,6 +147,37 @@ nmfkl_status nmfkl_sweep_F(nmfkl_ctx *ctx, int64_t sweep);
  * Synchronizes and reports the device error flags as nmfkl_sweep_F. */
 nmfkl_status nmfkl_sweep_W(nmfkl_ctx *ctx, int64_t sweep);
 
+/* One half of Algorithm 1 over a contiguous range of its units: side 0
+ * updates the columns u0 <= j < u1 of F (W fixed), side 1 the rows u0 <= i <
+ * u1 of W (F fixed), each exactly as nmfkl_sweep_F / nmfkl_sweep_W would
+ * (the coordinate orders are keyed by the global unit index), and leaves
+ * every other unit as it was. The subproblems of a half are independent
+ * (Eq. 3), so ranks that own disjoint ranges covering all units and then
+ * exchange their updated units (see nmfkl_factor_unit_major) reproduce the
+ * unsharded half bit for bit. For side 1, *data_term (may be NULL) receives
+ * the FP64 sum over the range's rows of Eq. 1's data term
+ * sum_p [v_p log(v_p / (x_p + eps_div)) - v_p] at their final model values;
+ * summed over a partition of the rows and added to nmfkl_linear_term, it is
+ * Eq. 1 at the new W and F (for side 0 it is set to 0). EINVAL unless 0 <= u0
+ * <= u1 <= the half's unit count (an empty range does nothing). Synchronizes
+ * and reports the device error flags as nmfkl_sweep_F. */
+nmfkl_status nmfkl_sweep_range(nmfkl_ctx *ctx, int32_t side, int64_t sweep, int64_t u0, int64_t u1,
+                               double *data_term);
+
+/* Eq. 1's linear term sum_ij [W^T F]_ij = sum_k (sum_i W_ki)(sum_j F_kj) at
+ * the current W and F, FP64 (the zero entries of V contribute their model
+ * value). Synchronizes. */
+nmfkl_status nmfkl_linear_term(nmfkl_ctx *ctx, double *out);
+
+/* The context's device copy of W (side 1) or F (side 0) in its internal
+ * unit-major layout: *units rows (n or m) of *ld floats (ld = 4 ceil(r/4);
+ * row u holds the r entries of unit u, then zero padding). The pointer stays
+ * valid until nmfkl_set_data or nmfkl_destroy; the caller may read it and
+ * overwrite whole rows between calls (e.g. the rows other ranks updated),
+ * keeping the padding zero. Meant for exchanging a sharded half's units with
+ * a collective in place. */
+nmfkl_status nmfkl_factor_unit_major(nmfkl_ctx *ctx, int32_t side, float **ptr, int64_t *units, int32_t *ld);
+
 /* Limit of every bounded device wait of the context's kernels (a CTA of a
  * thread-block cluster waiting for its peers' partial sums), in SM clock
  * cycles; 0 restores the default (4e9, about 2 s). A wait that reaches the

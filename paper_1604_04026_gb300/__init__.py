@@ -72,6 +72,7 @@ class NMFKL:
                 raise ValueError("give r or params")
             params = default_params(r, **kw)
         self.params = params
+        self.device = int(device)
         self.n, self.m, self.r = int(n), int(m), int(params.r)
         h = ctypes.c_void_p()
         st = self._lib.nmfkl_create(ctypes.byref(params), self.n, self.m, device,
@@ -143,6 +144,33 @@ class NMFKL:
     def sweep(self, sweep: int):
         self.sweep_F(sweep)
         self.sweep_W(sweep)
+
+    def sweep_range(self, side: int, sweep: int, u0: int, u1: int) -> float:
+        """One half over the units u0 <= u < u1 (side 0: columns of F, 1: rows of
+        W); returns the range's Eq. 1 data term for side 1 (0.0 for side 0)."""
+        dt = ctypes.c_double()
+        self._check(self._lib.nmfkl_sweep_range(self._h, int(side), int(sweep), int(u0), int(u1), ctypes.byref(dt)),
+                    "sweep_range")
+        return dt.value
+
+    def linear_term(self) -> float:
+        """sum_k (sum_i W_ki)(sum_j F_kj): Eq. 1's term over all entries of W^T F."""
+        out = ctypes.c_double()
+        self._check(self._lib.nmfkl_linear_term(self._h, ctypes.byref(out)), "linear_term")
+        return out.value
+
+    def factor_unit_major(self, side: int):
+        """The device copy of F (side 0) or W (side 1), unit-major (units x ld
+        floats), as a CUDA tensor sharing the context's memory."""
+        import torch
+        ptr, units, ld = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int32()
+        self._check(self._lib.nmfkl_factor_unit_major(self._h, int(side), ctypes.byref(ptr), ctypes.byref(units),
+                                                      ctypes.byref(ld)), "factor_unit_major")
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (units.value, ld.value), "typestr": "<f4",
+                                        "data": (ptr.value, False), "version": 3, "strides": None}
+        return torch.as_tensor(_View(), device="cuda:%d" % self.device)
 
     def set_wait_limit(self, cycles: int):
         """Limit (SM clock cycles) of the bounded waits between cluster CTAs;

@@ -69,6 +69,10 @@ SIGNATURES = [
     ("nmfkl_sweep_F", c_i32, [c_vp, c_i64]),
     ("nmfkl_sweep_W", c_i32, [c_vp, c_i64]),
     ("nmfkl_set_wait_limit", c_i32, [c_vp, c_i64]),
+    ("nmfkl_sweep_range", c_i32, [c_vp, c_i32, c_i64, c_i64, c_i64, ctypes.POINTER(c_f64)]),
+    ("nmfkl_linear_term", c_i32, [c_vp, ctypes.POINTER(c_f64)]),
+    ("nmfkl_factor_unit_major", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_i64),
+                                        ctypes.POINTER(c_i32)]),
     ("nmfkl_objective", c_i32, [c_vp, ctypes.POINTER(c_f64), ctypes.POINTER(c_f64)]),
     ("nmfkl_fit", c_i32, [c_vp, c_i64, c_i32, c_f64, c_vp, ctypes.POINTER(c_i32)]),
     ("nmfkl_step", c_i32, [c_vp, c_i64, ctypes.POINTER(c_f64)]),

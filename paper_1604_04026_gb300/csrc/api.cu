@@ -569,6 +569,61 @@ nmfkl_status nmfkl_step(nmfkl_ctx *c, int64_t sweep, double *kl) {
     return step_impl(c, sweep, kl);
 }
 
+nmfkl_status nmfkl_sweep_range(nmfkl_ctx *c, int32_t side, int64_t sweep, int64_t u0, int64_t u1,
+                               double *data_term) {
+    if (!c || (side != 0 && side != 1)) return NMFKL_EINVAL;
+    if (!c->have_data) {
+        c->err = "no data: call nmfkl_set_data first";
+        return NMFKL_EINVAL;
+    }
+    const int64_t units = side == 0 ? c->m : c->n;
+    if (u0 < 0 || u1 < u0 || u1 > units) {
+        c->err = "sweep_range: need 0 <= u0 <= u1 <= units";
+        return NMFKL_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    nmfkl_status st = clear_flags(c);
+    if (st == NMFKL_OK && u1 > u0) st = run_half(c, side, sweep, nullptr, u0, u1);
+    double h = 0.0;
+    if (st == NMFKL_OK && side == 1 && u1 > u0) {
+        st = launch_range_sum(c, c->unit_obj + u0, u1 - u0, c->dscalar + 1);
+        if (st == NMFKL_OK &&
+            !cuda_ok(c, cudaMemcpyAsync(&h, c->dscalar + 1, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+                     "copy data term"))
+            st = NMFKL_ECUDA;
+    }
+    if (st == NMFKL_OK) st = read_flags(c);  // synchronizes
+    if (st == NMFKL_OK && data_term) *data_term = h;
+    return st;
+}
+
+nmfkl_status nmfkl_linear_term(nmfkl_ctx *c, double *out) {
+    if (!c || !out) return NMFKL_EINVAL;
+    cudaSetDevice(c->device);
+    nmfkl_status st = launch_colsum(c, c->Wt, c->n, c->sumW, c->dsum[0]);
+    if (st == NMFKL_OK) st = launch_colsum(c, c->Ft, c->m, c->sumF, c->dsum[1]);
+    if (st != NMFKL_OK) return st;
+    std::vector<double> sw(c->p.r), sf(c->p.r);
+    if (!cuda_ok(c, cudaMemcpyAsync(sw.data(), c->dsum[0], sizeof(double) * c->p.r, cudaMemcpyDeviceToHost, c->stream),
+                 "copy sumW") ||
+        !cuda_ok(c, cudaMemcpyAsync(sf.data(), c->dsum[1], sizeof(double) * c->p.r, cudaMemcpyDeviceToHost, c->stream),
+                 "copy sumF") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "linear term sync"))
+        return NMFKL_ECUDA;
+    double s = 0.0;
+    for (int k = 0; k < c->p.r; ++k) s += sw[k] * sf[k];
+    *out = s;
+    return NMFKL_OK;
+}
+
+nmfkl_status nmfkl_factor_unit_major(nmfkl_ctx *c, int32_t side, float **ptr, int64_t *units, int32_t *ld) {
+    if (!c || !ptr || (side != 0 && side != 1)) return NMFKL_EINVAL;
+    *ptr = side == 0 ? c->Ft : c->Wt;
+    if (units) *units = side == 0 ? c->m : c->n;
+    if (ld) *ld = c->ldr;
+    return NMFKL_OK;
+}
+
 nmfkl_status nmfkl_set_wait_limit(nmfkl_ctx *c, int64_t cycles) {
     if (!c || cycles < 0) return NMFKL_EINVAL;
     c->wait_cycles = cycles > 0 ? (long long)cycles : kDefaultWaitCycles;
@@ -771,7 +826,7 @@ int32_t nmfkl_plan_info(const nmfkl_ctx *c, nmfkl_bucket_info *out, int32_t cap)
                 out[i].block = b.block;
                 out[i].smem = (int64_t)b.smem;
                 out[i].ran_last = (c->used_sparse[side] == lp &&
-                                   (b.short_class < 0 || (b.group ? 1 : 0) == c->short_choice[side][b.short_class]))
+                                   (b.short_class < 0 || (b.group ? 1 : 0) == short_kernel(c, side, b.short_class)))
                                       ? 1
                                       : 0;
                 out[i].list_plan = lp;

@@ -283,6 +283,28 @@ void launch_colsum_raw(cudaStream_t stream, const float *At, int64_t rows, int l
     colsum_final_kernel<<<1, 256, 0, stream>>>(part, kColsumBlocks, ldr, r, out, out_d);
 }
 
+namespace {
+// Sum of x[0..n) in FP64 by one block, in a fixed order (strided partial sums,
+// then a tree over the threads).
+__global__ void range_sum_kernel(const double *x, int64_t n, double *out) {
+    __shared__ double part[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+}  // namespace
+
+nmfkl_status launch_range_sum(nmfkl_ctx *c, const double *x, int64_t n, double *out) {
+    range_sum_kernel<<<1, 1024, 0, c->stream>>>(x, n, out);
+    return cuda_ok(c, cudaGetLastError(), "range sum") ? NMFKL_OK : NMFKL_ECUDA;
+}
+
 nmfkl_status enqueue_fused_objective(nmfkl_ctx *c) {
     // sumF (FP64) is current from the W half; sumW changed in it, so sum W again.
     nmfkl_status st = launch_colsum(c, c->Wt, c->n, c->sumW, c->dsum[0]);

@@ -91,6 +91,8 @@ struct HalfArgs {
     // (plan_id) returns at once
     const int32_t *plan_sel;
     int32_t plan_id;
+    // if u1 > u0, only the units u0 <= u < u1 are updated (a shard of the half)
+    int64_t u0, u1;
     // bucket
     const int32_t *units;  // unit ids of this bucket, longest first
     int32_t count;
@@ -273,16 +275,22 @@ cudaError_t group_attributes(int optin);
 // device; the limit is process-wide per-function state).
 cudaError_t kernel_attributes(int device);
 nmfkl_status plan_side(nmfkl_ctx *c, int side);
-nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *sweep_dev = nullptr);
+nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *sweep_dev = nullptr, int64_t u0 = 0,
+                      int64_t u1 = 0);
 void free_plan(nmfkl_ctx *c);
 const char *kind_name(int kind);
 const char *bucket_name(const Bucket &b);
 // Kernel timer name of a bucket: "<kernel>/F" or "<kernel>/W" (static storage).
 const char *bucket_timer_name(const Bucket &b, int side);
+// The kernel (0 dense tile, 1 group) that runs short length class `cls` of
+// the list plan of `side`: the context's choice, if the plan holds it.
+int short_kernel(const nmfkl_ctx *c, int side, int cls);
 
 // aux.cu
 nmfkl_status launch_colsum(nmfkl_ctx *c, const float *At, int64_t rows, float *out, double *out_d);
 nmfkl_status launch_fused_objective(nmfkl_ctx *c, double *kl);
+// FP64 sum of x[0..n) into *out (device), one block, fixed order.
+nmfkl_status launch_range_sum(nmfkl_ctx *c, const double *x, int64_t n, double *out);
 // The fused objective's kernels alone (capturable); the value lands in c->dscalar[0].
 nmfkl_status enqueue_fused_objective(nmfkl_ctx *c);
 // colsum into caller buffers: part holds 1024 x ldr doubles.

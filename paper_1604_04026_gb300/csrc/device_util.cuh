@@ -160,6 +160,10 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
 
 // A bucket of the plan the half did not choose returns at once.
 __device__ __forceinline__ bool plan_skip(const HalfArgs &a) { return a.plan_sel && *a.plan_sel != a.plan_id; }
+// A unit outside the half's shard (when one is set) is left to another rank.
+__device__ __forceinline__ bool out_of_range(const HalfArgs &a, int64_t u) {
+    return a.u1 > a.u0 && (u < a.u0 || u >= a.u1);
+}
 // The sweep index of the half (from device memory in a captured step).
 __device__ __forceinline__ int64_t sweep_of(const HalfArgs &a) { return a.sweep_dev ? *a.sweep_dev : a.sweep; }
 

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(256) group_kernel(HalfArgs a) {
         int L = 0;
         if (work) {
             u = a.units[qi];
+            if (out_of_range(a, u)) work = false;
             base = a.ptr[u];
             L = (int)(a.ptr[u + 1] - base);
             if (L > LMAX || L < 0) {  // cannot happen with a consistent plan; refuse rather than overrun

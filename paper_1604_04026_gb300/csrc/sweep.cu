@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
         }
         if (qi >= count) break;
         const int64_t u = kMode == kModeFree ? (int64_t)qi : (int64_t)a.units[qi];
+        if (out_of_range(a, u)) continue;
         const int64_t base = a.ptr[u];
         const int L = (int)(a.ptr[u + 1] - base);
         const int64_t perm_unit = a.unit_ids ? a.unit_ids[u] : u;
@@ -467,6 +468,7 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
         const int qi = s_q;
         if (qi >= a.count) break;
         const int64_t u = a.units[qi];
+        if (out_of_range(a, u)) continue;
         const int64_t base = a.ptr[u];
         const int L = (int)(a.ptr[u + 1] - base);
         for (int k = threadIdx.x; k < ldr; k += kGiantNT) {
@@ -701,6 +703,7 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 
     for (int qi = cid; qi < a.count; qi += nclusters) {
         const int64_t u = a.units[qi];
+        if (out_of_range(a, u)) continue;  // uniform over the cluster
         const int64_t ubase = a.ptr[u];
         const int Lall = (int)(a.ptr[u + 1] - ubase);
         const int Lc = (Lall + (int)csize - 1) / (int)csize;
@@ -1137,6 +1140,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
         }
         if (qi >= count) break;
         const int64_t u = a.units[qi];
+        if (out_of_range(a, u)) continue;  // uniform over a cluster
         int64_t base = a.ptr[u];
         int L = (int)(a.ptr[u + 1] - base);
         const int64_t perm_unit = a.unit_ids ? a.unit_ids[u] : u;
@@ -1755,13 +1759,14 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
             b.nnz = gnnz[gk];
             b.lcap = info.lmax;
             b.short_class = gk;
-            b.block = 256;
-            const int gpb = b.block / info.g;
+            // groups per block: as many whole warps of groups as shared memory
+            // holds, up to 256 threads; a class whose groups do not fit keeps
+            // only its dense-tile alternative
+            int gpb = 256 / info.g;
+            while (gpb > 0 && group_block_smem(gk, r, ldr, gpb) > (size_t)optin) gpb -= 32 / info.g;
+            if (gpb <= 0) continue;
+            b.block = gpb * info.g;
             b.smem = group_block_smem(gk, r, ldr, gpb);
-            if (b.smem > (size_t)optin) {
-                c->err = "group plan: shared memory exceeds the device limit";
-                return NMFKL_EINVAL;
-            }
             int per_sm = 0;
             if (!cuda_ok(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, info.fn, b.block, b.smem),
                          "occupancy"))
@@ -1973,6 +1978,15 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
     return plan_side_sparse(c, side, ptr, order, optin);
 }
 
+// The kernel that runs a short length class of the list plan: the chosen one
+// when the plan has it (a group kind that cannot be resident is left out).
+int short_kernel(const nmfkl_ctx *c, int side, int cls) {
+    if (c->short_choice[side][cls] == 0) return 0;
+    for (const Bucket &b : c->plan_sparse[side])
+        if (b.group && b.short_class == cls) return 1;
+    return 0;
+}
+
 namespace {
 // Launches one bucket of a half on stream st.
 cudaError_t launch_bucket(const Bucket &b, HalfArgs &a, cudaStream_t st) {
@@ -2015,7 +2029,7 @@ __global__ void plan_select_kernel(const unsigned long long *dens, double denom,
 // then every bucket of the plans that may run, in order; a bucket of the plan
 // not chosen returns at once. With `sweep_dev` set the kernels read the sweep
 // index from it (a captured step), else they take `sweep`.
-nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *sweep_dev) {
+nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *sweep_dev, int64_t u0, int64_t u1) {
     const bool F = side == 0;
     const float *At = F ? c->Wt : c->Ft;
     float *X = F ? c->Ft : c->Wt;
@@ -2044,6 +2058,8 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *swee
     a.seed = c->p.seed;
     a.sweep = sweep;
     a.sweep_dev = sweep_dev;
+    a.u0 = u0;
+    a.u1 = u1;
     a.side = side;
     a.scratch = c->scratch;
     a.counters = c->counters;
@@ -2088,7 +2104,7 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *swee
         a.plan_id = lp;
         for (auto &b : lp ? c->plan_sparse[side] : c->plan[side]) {
             // the alternative of a short length class that was not chosen
-            if (b.short_class >= 0 && (b.group ? 1 : 0) != c->short_choice[side][b.short_class]) continue;
+            if (b.short_class >= 0 && (b.group ? 1 : 0) != short_kernel(c, side, b.short_class)) continue;
             a.units = b.d_units;
             a.count = b.count;
             a.queue = c->queues + side * kQueuesPerSide + qi++;

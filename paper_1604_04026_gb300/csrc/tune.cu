@@ -187,6 +187,9 @@ nmfkl_status nmfkl_autotune(nmfkl_ctx *c, int64_t sweep, int32_t reps, const cha
                 break;
             }
             double t[kShortClasses][2] = {};
+            bool has[kShortClasses][2] = {};
+            for (const Bucket &b : c->plan_sparse[side])
+                if (b.short_class >= 0) has[b.short_class][b.group ? 1 : 0] = true;
             for (int alt = 0; alt < 2 && st == NMFKL_OK; ++alt) {
                 for (int k = 0; k < kShortClasses; ++k) c->short_choice[side][k] = (int8_t)alt;
                 for (int rep = 0; rep < reps && st == NMFKL_OK; ++rep) {
@@ -212,8 +215,9 @@ nmfkl_status nmfkl_autotune(nmfkl_ctx *c, int64_t sweep, int32_t reps, const cha
                     continue;
                 }
                 ms[(side * 4 + k) * 2 + 0] = t[k][0] / reps;
-                ms[(side * 4 + k) * 2 + 1] = t[k][1] / reps;
-                choice[side][k] = t[k][1] < t[k][0] ? 1 : 0;
+                ms[(side * 4 + k) * 2 + 1] = has[k][1] ? t[k][1] / reps : -1.0;
+                // a group kind the plan left out (shared memory) is not a candidate
+                choice[side][k] = has[k][1] && t[k][1] < t[k][0] ? 1 : 0;
             }
         }
         cudaStreamSynchronize(c->stream);

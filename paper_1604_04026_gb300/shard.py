@@ -9,6 +9,11 @@ by (seed, sweep, side, unit), the result does not depend on the partition.
 
 Only the partition and the exchange live here; the per-unit work is the
 CUDA library's (or, in the CPU tests, the oracle's).
+
+One sharded step (sharded_step) is the whole hot path on P ranks: the F half
+on each rank's columns, an all-gather of F's unit-major rows, the W half on
+each rank's rows, an all-gather of W's rows, and Eq. 1 as the all-reduced sum
+of the ranks' data terms plus the linear term sum_k sumW_k sumF_k.
 """
 from __future__ import annotations
 
@@ -53,3 +58,38 @@ def gather_units(local, ranges, rank: int, group=None):
     out = [torch.empty_like(buf) for _ in range(world)]
     dist.all_gather(out, buf, group=group)
     return torch.cat([out[k][: h - l] for k, (l, h) in enumerate(ranges)], dim=0)
+
+
+def exchange_units(view, ranges, rank: int, group=None):
+    """In-place all-gather of a factor's unit-major rows: `view` (units x ldr
+    tensor) holds this rank's updated rows in its range; afterwards it holds
+    every rank's."""
+    lo, hi = ranges[rank]
+    full = gather_units(view[lo:hi], ranges, rank, group)
+    view.copy_(full)
+
+
+def sharded_step(model, sweep: int, parts, rank: int, group=None) -> float:
+    """One step of Algorithm 1 sharded over the ranks of `group`: parts[0] are
+    the column ranges of the F half, parts[1] the row ranges of the W half (one
+    per rank, from `partition`). `model` offers sweep_range(side, sweep, lo,
+    hi) -> data term, factor_unit_major(side) -> tensor view and linear_term().
+    Returns Eq. 1 at the new W and F (FP64), the same on every rank."""
+    import torch
+    import torch.distributed as dist
+
+    lo, hi = parts[0][rank]
+    model.sweep_range(0, sweep, lo, hi)
+    view = model.factor_unit_major(0)
+    exchange_units(view, parts[0], rank, group)
+    if view.is_cuda:
+        torch.cuda.synchronize(view.device)
+    lo, hi = parts[1][rank]
+    data = model.sweep_range(1, sweep, lo, hi)
+    view = model.factor_unit_major(1)
+    exchange_units(view, parts[1], rank, group)
+    t = torch.tensor([data], dtype=torch.float64, device=view.device)
+    dist.all_reduce(t, group=group)
+    if view.is_cuda:
+        torch.cuda.synchronize(view.device)
+    return float(t.item()) + model.linear_term()

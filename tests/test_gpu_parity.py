@@ -160,18 +160,19 @@ def _check_halves(V, W0, F0, Fg, Fo, Wg, Wo, F1, p, fraction=None, obj_rel=OBJ_R
 
 def test_designed_lengths_reach_every_list_class(designed):
     """The designed lengths put units into every reachable class of the list
-    plan on both halves: the sub-warp group kernels for units of at most 256
-    nonzeros, then the list classes (the tight parity test above then covers
-    each of them)."""
+    plan on both halves: both alternatives for units of at most 256 nonzeros
+    (the dense-tile warp kernels and the sub-warp group kernels), then the
+    list classes (the tight parity tests cover each of them)."""
     r = 16
     W0, F0 = start(designed, r, seed=2)
     m = model(designed, W0, F0, params(r, seed=5, list_mode=2))
-    want = {"group_g4_l32", "group_g8_l64", "group_g8_l128", "group_g16_l256", "sparse_warp", "sparse_warp_1k",
-            "sparse_cta128", "sparse_cta256", "sparse_cta512", "sparse_cluster2"}
+    want = {"group_g4_l32", "group_g8_l64", "group_g8_l128", "group_g16_l256", "sweep_warp_k1", "sweep_warp_k2",
+            "sweep_warp_k4", "sweep_warp_k8", "sparse_warp", "sparse_warp_1k", "sparse_cta128", "sparse_cta256",
+            "sparse_cta512", "sparse_cluster2"}
     for side in (0, 1):
         kinds = {b["kernel"] for b in m.plan() if b["side"] == side and b["list_plan"]}
         assert want <= kinds, (side, want - kinds)
-        assert not kinds & {"sweep_warp_k1", "sweep_warp_k8", "sweep_warp_k16", "sweep_cta128_k8"}, kinds
+        assert not kinds & {"sweep_warp_k16", "sweep_cta128_k8"}, kinds
     m.close()
 
 
