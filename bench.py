@@ -40,6 +40,8 @@ WORKLOADS = {
                   "m=1,000,000 docs, Zipf(1.1)/Dirichlet(0.1), lognormal mean 150 tokens"),
     "docs": dict(n=30_000, m=100_000, K=50, desc="document-like corpus: n=30,000 words, m=100,000 docs, "
                  "Zipf(1.1)/Dirichlet(0.1), lognormal mean 150 tokens"),
+    "digits": dict(n=784, m=60_000, K=30, desc="dense-ish image set shaped like the paper's Digits: 784 pixels x "
+                   "60,000 images, 19% nonzero, intensities 1..255 (Dirichlet mixtures of blob strokes)"),
 }
 METRIC = "nnz*r coordinate updates/s per sweep"
 UNIT = "updates/s"
@@ -66,6 +68,8 @@ def parse():
     ap.add_argument("--list-mode", type=int, default=0, choices=[0, 1, 2],
                     help="coordinate loop: 0 chosen per half from the density, 1 dense tile, 2 sparse lists")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--reg", type=str, default="0,0,0,0",
+                    help="a1,b1,a2,b2: the L2 and L1 weights on W and on F of Eq. 2 (default none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shard", action="store_true",
@@ -85,6 +89,12 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def reg_kw(args):
+    """The Eq. 2 weights of --reg as library parameters."""
+    a1, b1, a2, b2 = (float(x) for x in args.reg.split(","))
+    return dict(alpha_W=a1, beta_W=b1, alpha_F=a2, beta_F=b2)
 
 
 def algorithmic_bytes(nnz, units, r):
@@ -198,6 +208,8 @@ def ncu_traffic(kernel, half, r, bucket_nnz):
 def make_corpus(args, threads):
     from paper_1604_04026_gb300 import synth
     w = WORKLOADS[args.workload]
+    if args.workload == "digits":
+        return synth.digits(w["m"], K=w["K"], seed=args.seed)
     return synth.docs(w["n"], w["m"], w["K"], seed=args.seed, threads=threads)
 
 
@@ -286,7 +298,7 @@ def run_ours(args):
             pg.barrier()
         torch.cuda.synchronize()
 
-    model = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local, list_mode=args.list_mode)
+    model = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local, list_mode=args.list_mode, **reg_kw(args))
     model.set_data(V)
     model.init()
     sweep = 0
@@ -381,9 +393,12 @@ def run_ours(args):
     dom = max(sweep_kernels, key=lambda k: sweep_kernels[k][1])
     launches, dom_ms = sweep_kernels[dom]
     per_launch_ms = dom_ms / max(launches, 1)
-    dom_kernel, dom_half = dom.rsplit("/", 1)
+    # "<kernel>/<half>" or, for a dense-tile bucket the list plan runs, "<kernel>/<half>/list"
+    parts = dom.split("/")
+    dom_kernel, dom_half, dom_list = parts[0], parts[1], len(parts) > 2
     dom_side = 0 if dom_half == "F" else 1
-    dom_bucket = next(b for b in plan_all if b["kernel"] == dom_kernel and b["side"] == dom_side)
+    dom_bucket = next(b for b in plan_all if b["kernel"] == dom_kernel and b["side"] == dom_side
+                      and (b["list_plan"] == dom_list or b["kernel"].startswith(("sparse_", "group_"))))
     bytes_per_launch = algorithmic_bytes(dom_bucket["nnz"], dom_bucket["count"], r)
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     # a step moves each half's bytes once, whichever plan runs it (the dense
@@ -430,7 +445,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "n": V.n, "m": V.m, "r": r,
                        "nnz": V.nnz, "updates_per_step": U, "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU", "eq2_weights": reg_kw(args)},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -461,7 +476,7 @@ def e2e_run(args, V, nk, torch, local, barrier, pg):
     r = args.r
     barrier()
     t0 = time.perf_counter()
-    m = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local, list_mode=args.list_mode)
+    m = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local, list_mode=args.list_mode, **reg_kw(args))
     m.set_data(nnz=V.nnz, **pinned)
     m.init()
     for s in range(args.steps):
@@ -756,7 +771,7 @@ def run_shard(args):
     V = make_corpus(args, threads)
     r = args.r
     U = 2 * V.nnz * r
-    model = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local, list_mode=args.list_mode)
+    model = nk.NMFKL(V.n, V.m, r=r, seed=args.seed, device=local, list_mode=args.list_mode, **reg_kw(args))
     model.set_data(V)
     model.init()
     parts = [shard.partition(V.colptr, ws), shard.partition(V.rowptr, ws)]

@@ -1643,7 +1643,11 @@ const char *bucket_name(const Bucket &b) {
     return b.sparse ? kSparseKinds[b.kind].name : kKinds[b.kind].name;
 }
 
-// Kernel timer name of a bucket: "<kernel>/F" or "<kernel>/W" (static storage).
+// Kernel timer name of a bucket: "<kernel>/F" or "<kernel>/W", and for a
+// dense-tile bucket that the list plan runs, "<kernel>/F/list" or
+// "<kernel>/W/list" (static storage). Both plans' buckets are launched when
+// the plan is chosen on the device, and the plan not chosen returns at once:
+// the names keep those empty launches apart from the ones that ran.
 const char *bucket_timer_name(const Bucket &b, int side) {
     static const std::vector<std::string> names = [] {
         std::vector<std::string> v;
@@ -1651,11 +1655,15 @@ const char *bucket_timer_name(const Bucket &b, int side) {
             for (int i = 0; i < kNumKinds; ++i) v.push_back(std::string(kKinds[i].name) + (s ? "/W" : "/F"));
             for (int i = 0; i < kNumSparseKinds; ++i) v.push_back(std::string(kSparseKinds[i].name) + (s ? "/W" : "/F"));
             for (int i = 0; i < group_kind_count(); ++i) v.push_back(std::string(group_kind(i).name) + (s ? "/W" : "/F"));
+            for (int i = 0; i < kNumKinds; ++i) v.push_back(std::string(kKinds[i].name) + (s ? "/W/list" : "/F/list"));
         }
         return v;
     }();
-    const int per = kNumKinds + kNumSparseKinds + group_kind_count();
-    const int idx = b.group ? kNumKinds + kNumSparseKinds + b.kind : (b.sparse ? kNumKinds + b.kind : b.kind);
+    const int per = kNumKinds + kNumSparseKinds + group_kind_count() + kNumKinds;
+    const int idx = b.group ? kNumKinds + kNumSparseKinds + b.kind
+                            : (b.sparse ? kNumKinds + b.kind
+                                        : (b.borrowed ? kNumKinds + kNumSparseKinds + group_kind_count() + b.kind
+                                                      : b.kind));
     return names[side * per + idx].c_str();
 }
 

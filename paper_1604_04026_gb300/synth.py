@@ -12,6 +12,10 @@ this project, so every workload here is synthetic and seeded:
 * ``foldin_docs`` -- new documents for fold-in: distinct-word counts drawn
   from Pareto(x_m=5, alpha=1.5) truncated at 5000 by resampling, words drawn
   from the same corpus; also returns the K topic-word distributions.
+* ``digits`` -- a dense-ish image set shaped like the paper's Digits (MNIST:
+  784 pixels x 60,000 images, ~19% nonzero, intensities 1..255): each image
+  a Dirichlet mixture of stroke prototypes on the 28 x 28 grid, cut at the
+  density's quantile and quantized.
 * ``uniform_init`` -- FP32 Uniform(0, 1) starting factors.
 
 This module only draws random numbers and builds CSC/CSR storage; it holds
@@ -215,6 +219,47 @@ def foldin_docs(n: int, m: int, K: int, zipf_s: float = 1.1, dir_a: float = 0.1,
     topics = np.empty((K, n), dtype=np.float32)
     lib.synth_topics(n, K, zipf_s, seed, _ptr(topics))
     return topics, from_csc(n, m, colptr, rowidx, val)
+
+
+def digits(m: int = 60_000, K: int = 30, density: float = 0.19, alpha: float = 0.3, seed: int = 0,
+           side: int = 28, chunk: int = 8192) -> CountMatrix:
+    """Images as columns of a (side*side) x m count matrix, MNIST-shaped.
+
+    K prototypes, each the sum of three isotropic Gaussian blobs (sigma 1.5 to
+    3 pixels) centred uniformly in the middle 20 x 20 pixels; image j =
+    sum_k theta_jk P_k with theta_j ~ Dirichlet(alpha 1_K), scaled to a peak of
+    1; pixels at or below the (1 - density) quantile c of the intensities are
+    dropped and a kept intensity t maps to round(255 (t - c) / (1 - c)), at
+    least 1 (soft stroke edges, as in anti-aliased digits). Seeded; the
+    realized density is `density` up to sampling of the quantile."""
+    g = np.random.Generator(np.random.PCG64([seed, 0xD161]))
+    n = side * side
+    yy, xx = np.mgrid[0:side, 0:side]
+    P = np.zeros((K, n))
+    for k in range(K):
+        for _ in range(3):
+            cy, cx = g.uniform(4, side - 4, size=2)
+            s = g.uniform(1.5, 3.0)
+            P[k] += np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * s * s)).ravel()
+    theta = g.dirichlet(alpha * np.ones(K), size=m)  # m x K
+    # the threshold: the (1 - density) quantile over a sample of images
+    samp = theta[: min(m, 4096)] @ P
+    samp /= samp.max(axis=1, keepdims=True)
+    cut = float(np.quantile(samp, 1.0 - density))
+    cols, rows, vals = [], [], []
+    for j0 in range(0, m, chunk):
+        img = theta[j0:j0 + chunk] @ P  # images x n
+        img /= img.max(axis=1, keepdims=True)
+        jj, ii = np.nonzero(img > cut)
+        cols.append(jj + j0)
+        rows.append(ii)
+        vals.append(np.maximum(1.0, np.rint(255.0 * (img[jj, ii] - cut) / (1.0 - cut))))
+    cols = np.concatenate(cols)
+    rows = np.concatenate(rows).astype(np.int32)
+    vals = np.concatenate(vals).astype(np.float32)
+    colptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(cols, minlength=m), out=colptr[1:])
+    return from_csc(n, m, colptr, rows, vals)
 
 
 def uniform_init(r: int, cols: int, seed: int = 0, tag: int = 0) -> np.ndarray:

@@ -118,3 +118,27 @@ def test_full_size_sampled_parity(large):
     F1_32 = F1.astype(np.float32).astype(np.float64)
     rows = _sample_units(V.rowptr, 24, rng)
     _check_sampled(rows, V.rowptr, V.colidx, V.rval, F1_32, W0, oracle.rowsum(F1_32), W1g, p, 1)
+
+
+def test_full_size_sampled_parity_regularized(large):
+    """Eq. 2 with a1, a2, b1, b2 > 0 at the benchmark's size: the F half from
+    the Uniform start and the W half from the same start (W0, F0), sampled
+    columns and rows against the oracle's Algorithm 2 one by one."""
+    V = large
+    reg = dict(alpha_W=0.05, beta_W=0.02, alpha_F=0.1, beta_F=0.01)
+    p = nk.default_params(R, seed=SEED, **reg)
+    rng = np.random.default_rng(11)
+    W0 = oracle.uniform_init(SEED, 0, R, V.n)
+    F0 = oracle.uniform_init(SEED, 1, R, V.m)
+    with nk.NMFKL(V.n, V.m, params=p) as m:
+        m.set_data(V)
+        m.init()
+        m.sweep_F(0)
+        F1g = m.get_F()
+        m.init()
+        m.sweep_W(0)
+        W1g = m.get_W()
+    _check_sampled(_sample_units(V.colptr, 32, rng), V.colptr, V.rowidx, V.val, W0, F0, oracle.rowsum(W0), F1g,
+                   p, 0)
+    _check_sampled(_sample_units(V.rowptr, 16, rng), V.rowptr, V.colidx, V.rval, F0, W0, oracle.rowsum(F0), W1g,
+                   p, 1)

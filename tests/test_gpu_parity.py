@@ -206,10 +206,13 @@ def test_halves_tight_group_kernels(case, designed, docs_small):
 
 
 @pytest.mark.parametrize("list_mode", LIST_MODES)
-@pytest.mark.parametrize("case", ["c1", "docs_r37", "reg"])
+@pytest.mark.parametrize("case", ["c1", "docs_r37", "reg", "digits"])
 def test_halves_tight(case, docs_small, list_mode):
     if case == "c1":
         V, r, extra = synth.poisson_lowrank(1000, 500, 10, seed=0), 10, {}
+    elif case == "digits":
+        # dense-ish (19%) images: ~150 nonzeros per column, pixel rows of up to ~1,200
+        V, r, extra = synth.digits(m=1500, seed=2), 20, {}
     elif case == "docs_r37":
         V, r, extra = docs_small, 37, {}
     else:
@@ -304,12 +307,17 @@ def test_kl_trajectory_20_sweeps(case, docs_small, list_mode):
 
 
 @pytest.mark.parametrize("list_mode", LIST_MODES)
-@pytest.mark.parametrize("case", ["c1", "docs"])
+@pytest.mark.parametrize("case", ["c1", "docs", "digits"])
 def test_halves_paper_constants(case, docs_small, list_mode):
     """At eps_x = 0.1 a break or clamp decision can flip between FP32 and FP64
     for an entry sitting on its threshold: gate the fraction of entries and
     the per-unit objective."""
-    V, r = (synth.poisson_lowrank(1000, 500, 10, seed=0), 10) if case == "c1" else (docs_small, 20)
+    if case == "c1":
+        V, r = synth.poisson_lowrank(1000, 500, 10, seed=0), 10
+    elif case == "digits":
+        V, r = synth.digits(m=1500, seed=2), 20
+    else:
+        V, r = docs_small, 20
     W0, F0 = start(V, r, seed=6)
     p = params(r, seed=6, list_mode=list_mode)
     _check_halves(V, W0, F0, *_halves(V, W0, F0, p), p, fraction=0.995, obj_rel=1e-5,

@@ -90,3 +90,16 @@ def test_foldin_topics_are_zipf_laws():
         s = np.sort(t)[::-1]
         assert abs(s[0] / s[1] - 2.0 ** 1.1) < 0.05  # p(k) proportional to k^-1.1
     assert V.m == 200 and (np.diff(V.colptr) >= 1).all()
+
+
+def test_digits_shape_density_and_values():
+    """The Digits-like set: 784 x m, ~19% nonzero, integer intensities in
+    [1, 255], both layouts agree, and the draw is reproducible."""
+    V = synth.digits(m=3000, seed=4)
+    assert (V.n, V.m) == (784, 3000)
+    assert abs(V.nnz / (V.n * V.m) - 0.19) < 0.01
+    assert V.val.min() >= 1 and V.val.max() <= 255 and np.all(V.val == np.rint(V.val))
+    assert V.val.min() < 20  # soft stroke edges reach low intensities
+    assert np.array_equal(np.sort(V.rval), np.sort(V.val))
+    W = synth.digits(m=3000, seed=4)
+    assert np.array_equal(V.rowidx, W.rowidx) and np.array_equal(V.val, W.val)
