@@ -53,10 +53,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["sweep", "fit", "foldin", "serve"], default="sweep",
+    ap.add_argument("--mode", choices=["sweep", "fit", "foldin", "serve", "profile"], default="sweep",
                     help="sweep: the factorization step (default); fit: time to the KL target from the "
                          "random start; foldin: batched fold-in of new documents; serve: the request loop "
-                         "under Poisson arrivals")
+                         "under Poisson arrivals; profile: --warmup steps, then one half between "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--profile-side", choices=["F", "W"], default="F", help="profile: the half to capture")
     ap.add_argument("--kl-rel-tol", type=float, default=1e-4,
                     help="fit: stop when the KL objective changes by at most this, relative, in a sweep")
     ap.add_argument("--max-sweeps", type=int, default=50, help="fit: sweep limit")
@@ -744,6 +746,43 @@ def run_serve(args):
     return 0
 
 
+def run_profile(args):
+    """--warmup steps from the seeded start, then one half (--profile-side) of
+    the next sweep between cudaProfilerStart and cudaProfilerStop, with the
+    kernel timers on; prints the half's buckets (kernel, units, nonzeros) and
+    kernel times as one JSON line. Meant for small ncu captures of one kernel
+    at a steady state: ncu --profile-from-start off -k <kernel> -c <n>."""
+    import torch
+    import paper_1604_04026_gb300 as nk
+
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    threads = args.threads or os.cpu_count() or 1
+    V = make_corpus(args, threads)
+    model = nk.NMFKL(V.n, V.m, r=args.r, seed=args.seed, device=local, list_mode=args.list_mode, **reg_kw(args))
+    model.set_data(V)
+    model.init()
+    for s in range(args.warmup):
+        model.step(s)
+    side = 0 if args.profile_side == "F" else 1
+    model.set_timing(True)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    (model.sweep_F if side == 0 else model.sweep_W)(args.warmup)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    times = model.kernel_times(reset=True)
+    buckets = [{"kernel": b["kernel"], "list_plan": b["list_plan"], "units": b["count"], "nnz": b["nnz"],
+                "ran": b["ran_last"]} for b in model.plan() if b["side"] == side]
+    print(json.dumps({"mode": "profile", "workload": WORKLOADS[args.workload]["desc"], "r": args.r,
+                      "sweep": args.warmup, "half": args.profile_side, "buckets": buckets,
+                      "kernel_ms": {k: v for k, v in times.items() if v[0]}}), flush=True)
+    model.close()
+    return 0
+
+
 def run_shard(args):
     """The sharded method: every rank holds V and both factors; per step each
     rank runs the F half on its nonzero-balanced column range, the ranks
@@ -821,6 +860,8 @@ def main():
         return run_reference(args)
     if args.shard:
         return run_shard(args)
+    if args.mode == "profile":
+        return run_profile(args)
     if args.mode == "fit":
         return run_fit(args)
     if args.mode == "foldin":
