@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--reg", type=str, default="0,0,0,0",
                     help="a1,b1,a2,b2: the L2 and L1 weights on W and on F of Eq. 2 (default none)")
+    ap.add_argument("--eps-div", type=float, default=None,
+                    help="the guard added to [Ax]_i in divisions and logs (library default 1e-6)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shard", action="store_true",
@@ -94,9 +96,12 @@ def dist_env():
 
 
 def reg_kw(args):
-    """The Eq. 2 weights of --reg as library parameters."""
+    """The Eq. 2 weights of --reg (and --eps-div, when given) as library parameters."""
     a1, b1, a2, b2 = (float(x) for x in args.reg.split(","))
-    return dict(alpha_W=a1, beta_W=b1, alpha_F=a2, beta_F=b2)
+    kw = dict(alpha_W=a1, beta_W=b1, alpha_F=a2, beta_F=b2)
+    if args.eps_div is not None:
+        kw["eps_div"] = float(args.eps_div)
+    return kw
 
 
 def algorithmic_bytes(nnz, units, r):

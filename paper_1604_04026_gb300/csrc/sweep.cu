@@ -429,6 +429,197 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
 }
 
 // ---------------------------------------------------------------------------
+// Sub-warp groups on the dense tile: units of at most G*K nonzeros with G
+// lanes per unit (G < 32) and 32/G units per warp. The warp takes its units
+// together and visits their coordinates in step (each unit in its own order),
+// with one warp-wide barrier per coordinate so that every instruction serves
+// all of them; the group reductions are log2(G) shuffles. A one-warp group on
+// a unit of a few dozen nonzeros spends most of each evaluation on the
+// 32-lane reduction and the scalar Newton step, which here are shared by
+// 32/G units. Staging and the tile ring are those of sweep_kernel.
+// ---------------------------------------------------------------------------
+template <int G, int K>
+__host__ __device__ constexpr int sub_min_blocks() {
+    return K <= 4 ? 3 : 2;
+}
+
+template <int G, int K, int D>
+__global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(HalfArgs a) {
+    static_assert(G == 4 || G == 8 || G == 16, "sub-warp groups of 4, 8 or 16 lanes");
+    if (plan_skip(a)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kPerWarp = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int glane = lane & (G - 1);
+    const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
+    const int group_in_block = threadIdx.x / G;
+    const int groups_per_block = blockDim.x / G;
+    const int group_global = blockIdx.x * groups_per_block + group_in_block;
+
+    const int r = a.r, ldr = a.ldr;
+    const RingLayout lay = ring_layout(r, ldr, G, K, D, false);
+    unsigned char *gs = smem_raw + (size_t)group_in_block * lay.bytes;
+    uint8_t *perm = gs;
+    float *x_init = reinterpret_cast<float *>(gs + 256);
+    float *x_out = x_init + ldr;
+    uint64_t *words = reinterpret_cast<uint64_t *>(gs + lay.aux_off);
+    int *xpos = reinterpret_cast<int *>(gs + lay.xpos_off);
+    float *myring = reinterpret_cast<float *>(gs + lay.ring_off) + glane;  // slot d, item s at [(d*K + s)*G]
+
+    float *tile = a.scratch + (int64_t)group_global * a.slot_floats;
+    const int lcap = a.lcap;
+    const float eps_div = a.eps_div;
+    const int count = a.count_dev ? *a.count_dev : a.count;
+    const int64_t sweep = sweep_of(a);
+    Tally tally;
+
+    for (;;) {
+        __syncwarp();
+        int q = 0;
+        if (lane == 0) q = atomicAdd(a.queue, kPerWarp);
+        q = __shfl_sync(kFull, q, 0);
+        if (q >= count) break;
+        // a group without a unit (the last batch) still runs the warp-wide
+        // coordinate loop, without work
+        const int qi = q + lane / G;
+        bool work = qi < count;
+        int64_t u = 0, base = 0;
+        int L = 0;
+        if (work) {
+            u = a.units[qi];
+            if (out_of_range(a, u)) {
+                work = false;
+            } else {
+                base = a.ptr[u];
+                L = (int)(a.ptr[u + 1] - base);
+                if (L > G * K || L < 0) {  // cannot happen with a consistent plan; refuse rather than overrun
+                    if (glane == 0) atomicOr(a.err, kErrLength);
+                    work = false;
+                    L = 0;
+                }
+            }
+        }
+        const int ks = work ? (L + G - 1) / G : 0;
+        if (work) {
+            for (int k = glane; k < ldr; k += G) {
+                const float xv = a.X[u * ldr + k];
+                x_init[k] = xv;
+                xpos[k] = xv > 0.f ? 1 : 0;
+            }
+        }
+        __syncwarp();
+
+        // ---- stage A rows, x_p, and the per-nonzero state (nonzero p = G s + glane)
+        float xr[K], vr[K], wr[K], qr[K];
+        int cr[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
+            if (s < ks) {
+                const int pl = G * s + glane;
+                int idx_l = 0;
+                float v_l = 0.f;
+                if (pl < L) {
+                    idx_l = a.idx[base + pl];
+                    v_l = a.val[base + pl];
+                }
+                const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
+                if (pl < L) {
+                    const float x_l = st.terms == 0 ? 0.f : st.x;
+                    xr[s] = x_l;
+                    cr[s] = st.terms;
+                    vr[s] = v_l;
+                    const float ri = recip(x_l + eps_div);
+                    wr[s] = v_l * ri;
+                    qr[s] = wr[s] * ri;
+                }
+            }
+        }
+        if (work) {
+            const int64_t perm_unit = a.unit_ids ? a.unit_ids[u] : u;
+            ids_words_warp(words, r, perm_unit, sweep, a.side, a.perm_mode, a.seed, glane, G);
+            __syncwarp(gmask);
+            if (glane == 0) fisher_yates(perm, words, r);
+        }
+        __syncwarp();
+
+        // ---- Algorithm 2 over the units' coordinates, in step
+        auto issue = [&](int pos) {
+            if (work && pos < r) {
+                const float *col = tile + (int64_t)perm[pos] * lcap + glane;
+                float *dst = myring + (pos % D) * K * G;
+#pragma unroll
+                for (int s = 0; s < K; ++s)
+                    if (s < ks) cp_async4(dst + s * G, col + G * s, glane + G * s < L ? 4 : 0);
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int i = 0; i < D - 1; ++i) issue(i);
+        for (int kk = 0; kk < r; ++kk) {
+            issue(kk + D - 1);
+            cp_async_wait<D - 1>();
+            if (work) {
+                const float *ac = myring + (kk % D) * K * G;
+                const int k = perm[kk];
+                auto eval = [&]() -> float2 {
+                    float sg = 0.f, sh = 0.f;
+#pragma unroll
+                    for (int s = 0; s < K; ++s) {
+                        if (s < ks) {
+                            const float av = ac[s * G];
+                            sg = fmaf(wr[s], av, sg);
+                            sh = fmaf(qr[s] * av, av, sh);
+                        }
+                    }
+#pragma unroll
+                    for (int o = G / 2; o > 0; o >>= 1) {
+                        sg += __shfl_xor_sync(gmask, sg, o);
+                        sh += __shfl_xor_sync(gmask, sh, o);
+                    }
+                    return make_float2(sg, sh);
+                };
+                auto update = [&](float d, int dc) {
+#pragma unroll
+                    for (int s = 0; s < K; ++s) {
+                        if (s < ks) {
+                            xr[s] = step_x(xr[s], ac[s * G], d, dc, cr[s]);
+                            const float ri = recip(xr[s] + eps_div);
+                            wr[s] = vr[s] * ri;
+                            qr[s] = wr[s] * ri;
+                        }
+                    }
+                };
+                const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
+                if (glane == 0) x_out[k] = xk;
+            }
+            __syncwarp();
+        }
+        cp_async_wait<0>();
+        if (work) {
+            if (a.unit_obj) {
+                float t = 0.f;
+#pragma unroll
+                for (int s = 0; s < K; ++s)
+                    if (s < ks) t += kl_term(vr[s], xr[s], eps_div);
+                double dt = (double)t;
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) dt += __shfl_xor_sync(gmask, dt, o);
+                if (glane == 0) a.unit_obj[u] = dt;
+            }
+            __syncwarp(gmask);
+            discard_tile(tile, r, L, lcap, glane, G);
+            for (int k = glane; k < r; k += G) {
+                const float xv = x_out[k];
+                if (!(xv == xv)) atomicOr(a.err, kErrNaN);
+                a.X[u * ldr + k] = xv;
+            }
+        }
+    }
+    if (glane == 0) flush_tally(a, tally);
+}
+
+// ---------------------------------------------------------------------------
 // Giant units (L beyond the register-resident buckets): one CTA per unit,
 // per-nonzero state in the group's global scratch slot:
 //   [T: r x lcap][x: lcap][v: lcap][w: lcap][q: lcap][terms: lcap]
@@ -1486,6 +1677,10 @@ struct KernelKind {
 
 constexpr int kClusterNT = 512, kClusterK = 12, kClusterD = 4;
 const KernelKind kKinds[] = {
+    // sub-warp groups (G lanes per unit) come first: for the lengths they hold
+    // they replace the one-warp kernels below
+    {(const void *)sweep_sub_kernel<8, 4, 4>, 8, 4, 1, 4, "sweep_sub_g8_k4"},
+    {(const void *)sweep_sub_kernel<16, 4, 4>, 16, 4, 1, 4, "sweep_sub_g16_k4"},
     {(const void *)sweep_kernel<32, 1, 4>, 32, 1, 1, 4, "sweep_warp_k1"},
     {(const void *)sweep_kernel<32, 2, 4>, 32, 2, 1, 4, "sweep_warp_k2"},
     {(const void *)sweep_kernel<32, 4, 4>, 32, 4, 1, 4, "sweep_warp_k4"},
@@ -1733,7 +1928,7 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
     // dense plan, and the group kinds, by length (one alternative per class runs)
     for (const Bucket &d : c->plan[side]) {
         const KernelKind &kk = kKinds[d.kind];
-        if (kk.cl == 1 && kk.k > 0 && kk.nt == 32 && (int64_t)kk.nt * kk.k <= kDenseBelow) {
+        if (kk.cl == 1 && kk.k > 0 && kk.nt <= 32 && (int64_t)kk.nt * kk.k <= kDenseBelow) {
             Bucket b = d;
             b.borrowed = true;
             b.short_class = group_kind_for_length((int64_t)kk.nt * kk.k);
@@ -1946,10 +2141,13 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
                                                  : ring_layout(r, ldr, b.nt, b.k, kKinds[kind].d, cta).bytes;
         int groups_per_block = 1;
         if (!cta) {
-            groups_per_block = 8;
-            while (groups_per_block > 1 && gbytes * groups_per_block > (size_t)optin) --groups_per_block;
+            // warp groups: up to 8 per block; sub-warp groups: whole warps of
+            // them, up to 256 threads
+            const int step = b.nt < 32 ? 32 / b.nt : 1;
+            groups_per_block = 256 / b.nt;
+            while (groups_per_block > step && gbytes * groups_per_block > (size_t)optin) groups_per_block -= step;
         }
-        b.block = cta ? b.nt : 32 * groups_per_block;
+        b.block = cta ? b.nt : b.nt * groups_per_block;
         b.smem = gbytes * (cta ? 1 : groups_per_block);
         if (b.smem > (size_t)optin) {
             c->err = "shared memory plan exceeds the device limit";

@@ -166,9 +166,9 @@ def test_designed_lengths_reach_every_list_class(designed):
     r = 16
     W0, F0 = start(designed, r, seed=2)
     m = model(designed, W0, F0, params(r, seed=5, list_mode=2))
-    want = {"group_g4_l32", "group_g8_l64", "group_g8_l128", "group_g16_l256", "sweep_warp_k1", "sweep_warp_k2",
-            "sweep_warp_k4", "sweep_warp_k8", "sparse_warp", "sparse_warp_1k", "sparse_cta128", "sparse_cta256",
-            "sparse_cta512", "sparse_cluster2"}
+    want = {"group_g4_l32", "group_g8_l64", "group_g8_l128", "group_g16_l256", "sweep_sub_g8_k4",
+            "sweep_sub_g16_k4", "sweep_warp_k4", "sweep_warp_k8", "sparse_warp", "sparse_warp_1k", "sparse_cta128",
+            "sparse_cta256", "sparse_cta512", "sparse_cluster2"}
     for side in (0, 1):
         kinds = {b["kernel"] for b in m.plan() if b["side"] == side and b["list_plan"]}
         assert want <= kinds, (side, want - kinds)
