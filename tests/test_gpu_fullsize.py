@@ -55,7 +55,7 @@ def _unit_scale(v, A, x, sumA, eps):
     return float(np.sum(v * (np.abs(np.log(v / (ax + eps))) + 1.0)) + sumA @ np.abs(x))
 
 
-def _check_sampled(units, ptr, idx, val, A_full, X0, sumA, got, p, side):
+def _check_sampled(units, ptr, idx, val, A_full, X0, sumA, got, p, side, name="full_size_sampled"):
     c = cfg_for(p, side)
     G, O, S = [], [], []
     for u in units:
@@ -84,7 +84,7 @@ def _check_sampled(units, ptr, idx, val, A_full, X0, sumA, got, p, side):
         assert (g >= 0).all()
     # columns are the sampled units; at the paper's constants a break or clamp
     # decision may flip between FP32 and FP64, so the gate is a fraction
-    rep = parity_report("full_size_sampled/%s" % ("F" if side == 0 else "W"), np.stack(G, axis=1),
+    rep = parity_report("%s/%s" % (name, "F" if side == 0 else "W"), np.stack(G, axis=1),
                         np.stack(O, axis=1), slack=np.stack(S, axis=1))
     assert 1.0 - rep["beyond_cap"] / rep["entries"] >= 0.99, rep
 
@@ -139,6 +139,6 @@ def test_full_size_sampled_parity_regularized(large):
         m.sweep_W(0)
         W1g = m.get_W()
     _check_sampled(_sample_units(V.colptr, 32, rng), V.colptr, V.rowidx, V.val, W0, F0, oracle.rowsum(W0), F1g,
-                   p, 0)
+                   p, 0, name="full_size_sampled_regularized")
     _check_sampled(_sample_units(V.rowptr, 16, rng), V.rowptr, V.colidx, V.rval, F0, W0, oracle.rowsum(F0), W1g,
-                   p, 1)
+                   p, 1, name="full_size_sampled_regularized")
