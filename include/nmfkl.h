@@ -51,7 +51,8 @@ typedef enum {
     NMFKL_ENUMERIC = 4,  /* NaN or Inf in the objective */
     NMFKL_ETIMEOUT = 5,  /* a bounded device wait gave up */
     NMFKL_EBUSY = 6,     /* not admissible now (serving) */
-    NMFKL_ENOTCONV = 7   /* max_sweeps reached before the tolerance */
+    NMFKL_ENOTCONV = 7,  /* max_sweeps reached before the tolerance */
+    NMFKL_ECANCELED = 8  /* a serving request withdrawn before it ran */
 } nmfkl_status;
 
 /* Parameters of Algorithms 1 and 2. nmfkl_default_params fills the defaults. */
@@ -276,6 +277,21 @@ nmfkl_status nmfkl_set_timing(nmfkl_ctx *ctx, int32_t enable);
 int32_t nmfkl_kernel_times(nmfkl_ctx *ctx, const char **names, int64_t *launches, double *ms,
                            int32_t cap, int32_t reset);
 
+/* Per-step metrics: with a path set, every step (nmfkl_step, and each sweep
+ * of nmfkl_fit) appends one JSON line to that file:
+ *   {"sweep", "kl" (Eq. 1 at the new factors), "ms" (device time of the
+ *    step), "updates_per_s" (2 nnz r / time), "gb_per_s" (algorithmic bytes of
+ *    the step / time: per half each nonzero's index, value and factor row,
+ *    each unit's r-vector read and written and its offset), "evals_per_coord"
+ *    and "steps_per_coord" (derivative evaluations and Newton steps of
+ *    Algorithm 2 per coordinate), "cap_hits", "zeros_W_pct", "zeros_F_pct"
+ *    (exact zeros, the measure of Table 2), "plan" (["dense"|"list"] per
+ *    half), "density" (fixed factor's density at the nonzeros, per half)}.
+ * The line costs a synchronization, two counting kernels and a small copy
+ * after the step, outside its timed span. NULL or "" stops writing. EINVAL if
+ * the file cannot be opened for appending. */
+nmfkl_status nmfkl_set_metrics(nmfkl_ctx *ctx, const char *path);
+
 /* Launch plans of the sweep kernels: one entry per length bucket, half and
  * plan (each half has a dense-tile plan and a sparse-list plan; the list plan
  * keeps the dense-tile buckets of its shortest units). */
@@ -480,6 +496,14 @@ nmfkl_status nmfkl_server_poll(nmfkl_server *s, uint64_t ticket, nmfkl_result *r
 
 /* Blocks until the request is done, then as poll. */
 nmfkl_status nmfkl_server_wait(nmfkl_server *s, uint64_t ticket, nmfkl_result *res);
+
+/* Withdraws a request that still waits in the queue: it never runs, its
+ * outputs are left untouched, and it is collected like any other (poll or
+ * wait give OK with result status NMFKL_ECANCELED). A request already running
+ * or done cannot be withdrawn: EBUSY, and it completes as usual. EINVAL for
+ * an unknown or already collected ticket. (Serving only; the paper has no
+ * counterpart.) */
+nmfkl_status nmfkl_server_cancel(nmfkl_server *s, uint64_t ticket);
 
 /* Queue length, charged memory, and how many fold-in batches have run and
  * how many requests they held. */

@@ -314,6 +314,11 @@ class NMFKL:
     def set_timing(self, enable: bool = True):
         self._check(self._lib.nmfkl_set_timing(self._h, int(enable)), "set_timing")
 
+    def set_metrics(self, path=None):
+        """Appends one JSON line per step to `path` (None stops): objective,
+        device time, throughput, work per coordinate, zeros of W and F."""
+        self._check(self._lib.nmfkl_set_metrics(self._h, path.encode() if path else None), "set_metrics")
+
     def kernel_times(self, reset: bool = False) -> dict:
         cap = 64
         names = (ctypes.c_char_p * cap)()
@@ -413,6 +418,17 @@ class Server:
             raise NMFKLError(st, "wait")
         t._set(res)
         return t
+
+    def cancel(self, t: Ticket) -> bool:
+        """Withdraws a request that still waits: True if it was withdrawn (it
+        is then collected by poll/wait with status ECANCELED), False if it is
+        already running or done."""
+        st = self._lib.nmfkl_server_cancel(self._h, t.id)
+        if st == 6:
+            return False
+        if st != 0:
+            raise NMFKLError(st, "cancel")
+        return True
 
     def stats(self) -> dict:
         x = _native.ServerStats()

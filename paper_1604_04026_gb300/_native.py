@@ -13,7 +13,7 @@ from . import _build
 c_i32, c_i64, c_u64, c_f64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ETIMEOUT",
-                6: "EBUSY", 7: "ENOTCONV"}
+                6: "EBUSY", 7: "ENOTCONV", 8: "ECANCELED"}
 
 
 class Params(ctypes.Structure):
@@ -90,6 +90,7 @@ SIGNATURES = [
     ("nmfkl_set_state", c_i32, [c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     ("nmfkl_get_counters", c_i32, [c_vp, ctypes.POINTER(Counters), c_i32]),
     ("nmfkl_set_timing", c_i32, [c_vp, c_i32]),
+    ("nmfkl_set_metrics", c_i32, [c_vp, ctypes.c_char_p]),
     ("nmfkl_kernel_times", c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32]),
     ("nmfkl_debug_perm", c_i32, [c_vp, c_i64, c_i32, c_i64, c_vp, c_vp]),
     ("nmfkl_server_default_cfg", None, [ctypes.POINTER(ServerCfg)]),
@@ -99,6 +100,7 @@ SIGNATURES = [
     ("nmfkl_server_poll", c_i32, [c_vp, c_u64, ctypes.POINTER(Result)]),
     ("nmfkl_server_wait", c_i32, [c_vp, c_u64, ctypes.POINTER(Result)]),
     ("nmfkl_server_stats", c_i32, [c_vp, ctypes.POINTER(ServerStats)]),
+    ("nmfkl_server_cancel", c_i32, [c_vp, c_u64]),
     ("nmfkl_server_destroy", None, [c_vp]),
     ("nmfkl_sweep_F_noalloc", c_i32, [ctypes.POINTER(Params), c_i64, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp,
                                       c_vp, c_i64, c_vp]),

@@ -151,6 +151,7 @@ const char *nmfkl_status_string(nmfkl_status s) {
         case NMFKL_ETIMEOUT: return "device wait timed out";
         case NMFKL_EBUSY: return "busy";
         case NMFKL_ENOTCONV: return "not converged";
+        case NMFKL_ECANCELED: return "canceled";
     }
     return "unknown status";
 }
@@ -228,6 +229,7 @@ void nmfkl_destroy(nmfkl_ctx *c) {
     cudaFree(c->crow_cnt); cudaFree(c->crow_k); cudaFree(c->crow_a);
     for (auto &pd : c->pending) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    free_metrics(c);
     delete c;
 }
 
@@ -237,6 +239,7 @@ nmfkl_status nmfkl_set_data(nmfkl_ctx *c, int64_t nnz, const int64_t *colptr, co
                             const float *val, const int64_t *rowptr, const int32_t *colidx, const float *rval,
                             int32_t mem_kind) {
     if (!c) return NMFKL_EINVAL;
+    TraceRange trace("nmfkl set_data");
     if (nnz < 0 || nnz > INT32_MAX * 8LL || !colptr || (nnz > 0 && (!rowidx || !val)) ||
         (mem_kind != 0 && mem_kind != 1)) {
         c->err = "set_data: bad arguments";
@@ -494,8 +497,10 @@ nmfkl_status build_step_graph(nmfkl_ctx *c) {
 // objective, the device flags and the plans chosen, read back in one
 // synchronization. Flags take precedence over a non-finite objective.
 nmfkl_status step_impl(nmfkl_ctx *c, int64_t sweep, double *kl) {
+    TraceRange trace("nmfkl step");
     nmfkl_status st = clear_flags(c);
     if (st != NMFKL_OK) return st;
+    if (c->metrics && !cuda_ok(c, cudaEventRecord(c->mev[0], c->stream), "metrics event")) return NMFKL_ECUDA;
     if (c->timing) {
         st = enqueue_step(c, sweep, nullptr);
     } else {
@@ -510,6 +515,7 @@ nmfkl_status step_impl(nmfkl_ctx *c, int64_t sweep, double *kl) {
         }
     }
     if (st != NMFKL_OK) return st;
+    if (c->metrics && !cuda_ok(c, cudaEventRecord(c->mev[1], c->stream), "metrics event")) return NMFKL_ECUDA;
     double h = 0.0;
     if (!cuda_ok(c, cudaMemcpyAsync(&h, c->dscalar, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy objective"))
         return NMFKL_ECUDA;
@@ -520,7 +526,7 @@ nmfkl_status step_impl(nmfkl_ctx *c, int64_t sweep, double *kl) {
         c->err = "objective is not finite";
         return NMFKL_ENUMERIC;
     }
-    return NMFKL_OK;
+    return write_metrics(c, sweep, h);
 }
 
 }  // namespace
@@ -535,6 +541,7 @@ nmfkl_status nmfkl_fit(nmfkl_ctx *c, int64_t sweep0, int32_t max_sweeps, double 
         return NMFKL_EINVAL;
     }
     cudaSetDevice(c->device);
+    TraceRange trace("nmfkl fit");
     double prev = 0.0;
     nmfkl_status st = launch_objective(c, &prev, nullptr);
     if (st != NMFKL_OK) return st;
@@ -692,6 +699,7 @@ nmfkl_status foldin_impl(nmfkl_ctx *c, int64_t m_new, int64_t nnz, const int64_t
                          const float *val, const int64_t *doc_ids, const float *F0,
                          const std::vector<FoldSegment> *segs, float *F_out, double rel_tol, int32_t max_sweeps,
                          int32_t *sweeps_done, double *doc_obj, int32_t launch_mode, int32_t mem_kind) {
+    TraceRange trace("nmfkl foldin");
     if (!c) return NMFKL_EINVAL;
     if (m_new < 0 || m_new > INT32_MAX || nnz < 0 || !colptr || (nnz > 0 && (!rowidx || !val)) || !F_out ||
         !(rel_tol >= 0) || max_sweeps < 0 || launch_mode < 0 || launch_mode > 2 || (mem_kind != 0 && mem_kind != 1)) {

@@ -2,8 +2,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include <cstdio>
 #include <string>
 #include <vector>
 
@@ -117,6 +119,9 @@ struct HalfArgs {
 
 // One launch configuration of the sweep kernel family.
 struct Bucket {
+    // floats from the scratch base to this bucket's slots: every bucket of a
+    // plan has slots of its own, since consecutive buckets may run at once
+    int64_t scratch_off = 0;
     bool sparse = false;  // kernel table: the sparse-list kinds (else the dense-tile kinds)
     bool group = false;   // kernel table: the sub-warp group kinds (lists of compressed rows)
     int kind;         // index into the kernel table
@@ -228,9 +233,13 @@ struct nmfkl_ctx {
     double density[2] = {-1.0, -1.0};           // last measured density per half
     int used_sparse[2] = {-1, -1};              // which plan the last half ran
     // list plan: per half and short length class, 0 = dense-tile warp kernel,
-    // 1 = group kernel over the compressed rows (set by nmfkl_set_short_kernels
-    // or the autotuner)
+    // 1 = group kernel over the compressed rows (set by nmfkl_set_plan_choice
+    // or nmfkl_autotune)
     int8_t short_choice[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    // plans with cluster buckets launch longest first, each bucket allowed to
+    // overlap the previous one's tail (set per half and plan at planning)
+    bool pdl = true;
+    bool overlap[2][2] = {{false, false}, {false, false}};
     nmfkl::FoldState *fold = nullptr;
     // timing
     bool timing = false;
@@ -238,12 +247,33 @@ struct nmfkl_ctx {
     std::vector<cudaEvent_t> ev_pool;
     struct Pending { int timer; cudaEvent_t a, b; };
     std::vector<Pending> pending;
+    // per-step metrics (nmfkl_set_metrics): the file, the events around a
+    // step, zero counts of W and F (device), the work counters at the last line
+    std::FILE *metrics = nullptr;
+    cudaEvent_t mev[2] = {nullptr, nullptr};
+    unsigned long long *zeros_dev = nullptr;
+    unsigned long long mprev[4] = {0, 0, 0, 0};
 };
 
 namespace nmfkl {
 
 // Error helpers (host).
 bool cuda_ok(nmfkl_ctx *c, cudaError_t e, const char *what);
+
+// A named NVTX range over a host-side phase (a step, a half, fold-in, a
+// serving batch): profilers show it as a span; without one attached the
+// push and pop cost a few nanoseconds.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
+// trace.cu: one metrics line after a step whose work lies between c->mev[0]
+// and c->mev[1] (no-op without a metrics file); freeing its state.
+nmfkl_status write_metrics(nmfkl_ctx *c, int64_t sweep, double kl);
+void free_metrics(nmfkl_ctx *c);
 
 // Timing hooks around every kernel launch.
 int timer_begin(nmfkl_ctx *c, const char *name);

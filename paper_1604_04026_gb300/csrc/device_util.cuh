@@ -78,6 +78,115 @@ __device__ __forceinline__ float recip(float x) {
     return y;
 }
 
+// The rest of step_x once x + d A_pk has been formed (by a packed fma).
+__device__ __forceinline__ float finish_x(float x, float av, int dc, int &terms) {
+    if (dc == 0) return fmaxf(x, 0.f);
+    if (av > 0.f) terms += dc;
+    return terms == 0 ? 0.f : fmaxf(x, 0.f);
+}
+
+// Packed FP32 pairs: one instruction performs two IEEE operations, each half
+// rounded exactly as the scalar fmaf / multiplication / addition (sm_100 and
+// later), so the per-nonzero loops issue half the arithmetic instructions.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long v;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
+    return v;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return make_float2(lo, hi);
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// One lane's share of an evaluation (Eq. Partial) over its staged nonzeros
+// s < ks: (sum_s w_s a_s, sum_s q_s a_s^2) with a_s = ac[s * STRIDE]. For even
+// K the even and odd s are accumulated in the two halves of packed registers
+// and added at the end; the entry after the last (s = ks, when ks is odd)
+// must hold a finite value, its w and q being 0.
+template <int K, int STRIDE>
+__device__ __forceinline__ float2 lane_sums(const float *ac, const float (&wr)[K], const float (&qr)[K], int ks) {
+    if constexpr (K % 2 == 1) {
+        float sg = 0.f, sh = 0.f;
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (s < ks) {
+                const float av = ac[s * STRIDE];
+                sg = fmaf(wr[s], av, sg);
+                sh = fmaf(qr[s] * av, av, sh);
+            }
+        }
+        return make_float2(sg, sh);
+    } else {
+        unsigned long long g = 0ull, h = 0ull;  // (+0, +0)
+#pragma unroll
+        for (int s = 0; s < K; s += 2) {
+            if (s < ks) {
+                const unsigned long long a2 = pack2(ac[s * STRIDE], ac[(s + 1) * STRIDE]);
+                g = ffma2(pack2(wr[s], wr[s + 1]), a2, g);
+                h = ffma2(fmul2(pack2(qr[s], qr[s + 1]), a2), a2, h);
+            }
+        }
+        const float2 gg = unpack2(g), hh = unpack2(h);
+        return make_float2(gg.x + gg.y, hh.x + hh.y);
+    }
+}
+
+// One lane's share of an update (Algorithm 2, "Update Ax"): x_s += d a_s on
+// its staged nonzeros s < ks with the positive-term counts, then w_s and q_s
+// refreshed; the same operations, in the same rounding, as step_x and the
+// scalar refresh. For even K the entry after the last (s = ks, ks odd) is
+// updated too: its a_s is 0 and its state stays 0.
+template <int K, int STRIDE>
+__device__ __forceinline__ void lane_update(const float *ac, float (&xr)[K], const float (&vr)[K], float (&wr)[K],
+                                            float (&qr)[K], int (&cr)[K], int ks, float d, int dc, float eps_div) {
+    if constexpr (K % 2 == 1) {
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (s < ks) {
+                xr[s] = step_x(xr[s], ac[s * STRIDE], d, dc, cr[s]);
+                const float ri = recip(xr[s] + eps_div);
+                wr[s] = vr[s] * ri;
+                qr[s] = wr[s] * ri;
+            }
+        }
+    } else {
+        const unsigned long long d2 = pack2(d, d), e2 = pack2(eps_div, eps_div);
+#pragma unroll
+        for (int s = 0; s < K; s += 2) {
+            if (s < ks) {
+                const float a0 = ac[s * STRIDE], a1 = ac[(s + 1) * STRIDE];
+                const float2 x = unpack2(ffma2(d2, pack2(a0, a1), pack2(xr[s], xr[s + 1])));
+                xr[s] = finish_x(x.x, a0, dc, cr[s]);
+                xr[s + 1] = finish_x(x.y, a1, dc, cr[s + 1]);
+                const float2 t = unpack2(fadd2(pack2(xr[s], xr[s + 1]), e2));
+                const unsigned long long ri = pack2(recip(t.x), recip(t.y));
+                const unsigned long long w2 = fmul2(pack2(vr[s], vr[s + 1]), ri);
+                const float2 w = unpack2(w2), q = unpack2(fmul2(w2, ri));
+                wr[s] = w.x;
+                wr[s + 1] = w.y;
+                qr[s] = q.x;
+                qr[s + 1] = q.y;
+            }
+        }
+    }
+}
+
 // Work counters of one thread (flushed once per kernel; a group processes far
 // fewer than 2^32 coordinates).
 struct Tally {
@@ -157,6 +266,20 @@ __device__ __forceinline__ float newton_coordinate(const HalfArgs &a, float xk, 
     }
     return xk;
 }
+
+// Programmatic dependent launch between the buckets of a half. The buckets
+// work on disjoint units and read only what was complete before the first of
+// them started, so a bucket lets the next one start at once
+// (launch_dependents at entry): the next bucket's blocks take SMs as the
+// current one's tail frees them, or SMs its clusters leave idle. Before it
+// exits, every block waits for the previous bucket to complete (wait), so
+// that the last bucket's completion still implies every earlier one's, and
+// whatever follows the half in stream order sees all of its results. Both
+// instructions are no-ops in a kernel launched without the attribute.
+struct PdlScope {
+    __device__ __forceinline__ PdlScope() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+    __device__ __forceinline__ ~PdlScope() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+};
 
 // A bucket of the plan the half did not choose returns at once.
 __device__ __forceinline__ bool plan_skip(const HalfArgs &a) { return a.plan_sel && *a.plan_sel != a.plan_id; }

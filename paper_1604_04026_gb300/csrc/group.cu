@@ -140,6 +140,7 @@ __device__ __forceinline__ void unit_nonzeros(const int32_t *__restrict__ idx, c
 
 template <int G, int LMAX>
 __global__ void __launch_bounds__(256) group_kernel(HalfArgs a) {
+    PdlScope pdl;
     if (plan_skip(a)) return;
     static_assert(G >= 4 && G <= 32 && (G & (G - 1)) == 0, "G: 4, 8, 16 or 32 lanes");
     static_assert(LMAX <= 256, "list entries hold p in 8 bits");

@@ -14,6 +14,7 @@
 // orders) and their own starting draw.
 #include "common.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <condition_variable>
@@ -232,10 +233,13 @@ void worker(nmfkl_server *s, int slot) {
         s->cv_work.notify_all();
         nmfkl_status st;
         std::string msg;
-        if (work.front()->kind == NMFKL_REQ_FOLDIN)
+        if (work.front()->kind == NMFKL_REQ_FOLDIN) {
+            TraceRange trace("serve fold-in batch");
             st = run_foldin_batch(s->fold_ctx[slot], work, msg);
-        else
+        } else {
+            TraceRange trace("serve fit");
             st = run_fit(s, s->streams[slot], work.front(), msg);
+        }
         {
             std::lock_guard<std::mutex> lk(s->mu);
             const auto now = Clock::now();
@@ -385,6 +389,28 @@ nmfkl_status nmfkl_server_wait(nmfkl_server *s, uint64_t ticket, nmfkl_result *r
     fill_result(q, res);
     delete q;
     s->reqs.erase(ticket);
+    return NMFKL_OK;
+}
+
+nmfkl_status nmfkl_server_cancel(nmfkl_server *s, uint64_t ticket) {
+    if (!s) return NMFKL_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return NMFKL_EINVAL;
+        ServerReq *q = it->second;
+        // only a request still in the queue: a worker that took it owns it
+        auto pos = std::find(s->pending.begin(), s->pending.end(), q);
+        if (q->done || pos == s->pending.end()) return NMFKL_EBUSY;
+        s->pending.erase(pos);
+        q->t_admit = q->t_done = Clock::now();
+        q->status = NMFKL_ECANCELED;
+        q->message = "canceled before it ran";
+        q->done = true;
+    }
+    s->cv_done.notify_all();
+    // the new head of the queue may be admissible now
+    s->cv_work.notify_all();
     return NMFKL_OK;
 }
 

@@ -140,6 +140,7 @@ constexpr int kModeHalf = 0, kModeFree = 1, kModeFold = 2;
 
 template <int NT, int K, int D, int kMode = kModeHalf>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) sweep_kernel(HalfArgs a) {
+    PdlScope pdl;
     if (plan_skip(a)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
@@ -222,6 +223,9 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
             }
         }
         const int ks = (L + NT - 1) / NT;
+        // ring entries filled per coordinate: for even K a whole number of
+        // pairs (the extra entry is zero-filled: its nonzeros lie past L)
+        const int ks2 = K % 2 == 0 ? ks + (ks & 1) : ks;
 
         for (int k = tid_g; k < ldr; k += NT) {
             const float xv = a.X[u * ldr + k];
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                     float *dst = myring + (pos % D) * K * NT;
 #pragma unroll
                     for (int s = 0; s < K; ++s)
-                        if (s < ks) cp_async4(dst + s * NT, col + NT * s, tid_g + NT * s < L ? 4 : 0);
+                        if (s < ks2) cp_async4(dst + s * NT, col + NT * s, tid_g + NT * s < L ? 4 : 0);
                 }
                 cp_async_commit();
             };
@@ -313,28 +317,10 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
                 const float *ac = myring + (kk % D) * K * NT;
                 const int k = perm[kk];
                 auto eval = [&]() -> float2 {
-                    float sg = 0.f, sh = 0.f;
-#pragma unroll
-                    for (int s = 0; s < K; ++s) {
-                        if (s < ks) {
-                            const float av = ac[s * NT];
-                            sg = fmaf(wr[s], av, sg);
-                            sh = fmaf(qr[s] * av, av, sh);
-                        }
-                    }
-                    return reduce(sg, sh);
+                    const float2 t = lane_sums<K, NT>(ac, wr, qr, ks);
+                    return reduce(t.x, t.y);
                 };
-                auto update = [&](float d, int dc) {
-#pragma unroll
-                    for (int s = 0; s < K; ++s) {
-                        if (s < ks) {
-                            xr[s] = step_x(xr[s], ac[s * NT], d, dc, cr[s]);
-                            const float ri = recip(xr[s] + eps_div);
-                            wr[s] = vr[s] * ri;
-                            qr[s] = wr[s] * ri;
-                        }
-                    }
-                };
+                auto update = [&](float d, int dc) { lane_update<K, NT>(ac, xr, vr, wr, qr, cr, ks, d, dc, eps_div); };
                 const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
                 if (tid_g == 0) x_out[k] = xk;
             }
@@ -446,6 +432,7 @@ __host__ __device__ constexpr int sub_min_blocks() {
 template <int G, int K, int D>
 __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(HalfArgs a) {
     static_assert(G == 4 || G == 8 || G == 16, "sub-warp groups of 4, 8 or 16 lanes");
+    PdlScope pdl;
     if (plan_skip(a)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kPerWarp = 32 / G;
@@ -500,6 +487,7 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
             }
         }
         const int ks = work ? (L + G - 1) / G : 0;
+        const int ks2 = K % 2 == 0 ? ks + (ks & 1) : ks;  // whole pairs, the extra entry zero-filled
         if (work) {
             for (int k = glane; k < ldr; k += G) {
                 const float xv = a.X[u * ldr + k];
@@ -550,7 +538,7 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
                 float *dst = myring + (pos % D) * K * G;
 #pragma unroll
                 for (int s = 0; s < K; ++s)
-                    if (s < ks) cp_async4(dst + s * G, col + G * s, glane + G * s < L ? 4 : 0);
+                    if (s < ks2) cp_async4(dst + s * G, col + G * s, glane + G * s < L ? 4 : 0);
             }
             cp_async_commit();
         };
@@ -563,15 +551,8 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
                 const float *ac = myring + (kk % D) * K * G;
                 const int k = perm[kk];
                 auto eval = [&]() -> float2 {
-                    float sg = 0.f, sh = 0.f;
-#pragma unroll
-                    for (int s = 0; s < K; ++s) {
-                        if (s < ks) {
-                            const float av = ac[s * G];
-                            sg = fmaf(wr[s], av, sg);
-                            sh = fmaf(qr[s] * av, av, sh);
-                        }
-                    }
+                    const float2 t = lane_sums<K, G>(ac, wr, qr, ks);
+                    float sg = t.x, sh = t.y;
 #pragma unroll
                     for (int o = G / 2; o > 0; o >>= 1) {
                         sg += __shfl_xor_sync(gmask, sg, o);
@@ -579,17 +560,7 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
                     }
                     return make_float2(sg, sh);
                 };
-                auto update = [&](float d, int dc) {
-#pragma unroll
-                    for (int s = 0; s < K; ++s) {
-                        if (s < ks) {
-                            xr[s] = step_x(xr[s], ac[s * G], d, dc, cr[s]);
-                            const float ri = recip(xr[s] + eps_div);
-                            wr[s] = vr[s] * ri;
-                            qr[s] = wr[s] * ri;
-                        }
-                    }
-                };
+                auto update = [&](float d, int dc) { lane_update<K, G>(ac, xr, vr, wr, qr, cr, ks, d, dc, eps_div); };
                 const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
                 if (glane == 0) x_out[k] = xk;
             }
@@ -627,6 +598,7 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
 constexpr int kGiantNT = 512;
 
 __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
+    PdlScope pdl;
     if (plan_skip(a)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kNW = kGiantNT / 32;
@@ -818,6 +790,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
 
 template <int NT, int K, int D>
 __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
+    PdlScope pdl;
     if (plan_skip(a)) return;  // uniform over the cluster: every CTA reads the same selection
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -1065,8 +1038,12 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
 // lists hold only its own nonzeros, so warps never touch each other's state.
 // (In a cluster each CTA does the same on its own slice of the unit.)
 // ---------------------------------------------------------------------------
-// list entries per lane prefetched into registers: warp groups, CTA groups
-constexpr int kSparseE = 4, kSparseECta = 8;
+// list entries per lane prefetched into registers: warp groups (8 for the
+// 513..1,024-nonzero compact class, whose lists on the W half run past four
+// entries per lane: 10.1 -> 9.6 ms per W half on the large corpus at a steady
+// state; the 257..512 class measured slower with 8 on the F half), CTA groups
+// (12 measured slower than 8)
+constexpr int kSparseE = 4, kSparseE1k = 8, kSparseECta = 8;
 
 constexpr int kSparseCapW = 256;  // list entries per warp staged in shared memory per coordinate
 
@@ -1137,6 +1114,7 @@ __host__ __device__ constexpr int sparse_min_blocks() {
 // CTAs.) Clusters take units from the bucket's queue, longest first.
 template <int NT, bool kSmemState, bool kCompact = false, bool kCluster = false>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kSmemState>())) sparse_kernel(HalfArgs a) {
+    PdlScope pdl;
     if (plan_skip(a)) return;  // uniform over a cluster: every CTA reads the same selection
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kCta = NT > 32;
@@ -1145,7 +1123,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
     constexpr int G = 32;
     static_assert(!kCluster || (kCta && kSmemState), "clusters split CTA groups with shared state");
     constexpr int kNW = NT / 32;
-    constexpr int E = kCta ? kSparseECta : kSparseE;
+    constexpr int E = kCta ? kSparseECta : (kCompact ? kSparseE1k : kSparseE);
     constexpr int CH = kCta ? 32 : G;   // lanes per chunk of nonzeros (a warp, or the group)
     constexpr int GS = kCta ? NT : G;   // threads per group
     const int lane = threadIdx.x & 31;
@@ -1745,8 +1723,11 @@ struct SparseKind {
     const char *name;
 };
 // List classes (units of more than kDenseBelow nonzeros): one warp per unit
-// up to 1,024 nonzeros, then one CTA of 128 / 256 / 512 threads per unit up
-// to 2,048 / 4,096 / kSliceCap nonzeros, then a cluster of 2, 3, 4, 6, 8 or
+// up to 1,024 nonzeros, then one CTA of 128 / 256 / 256 (compact state) /
+// 512 threads per unit up to 2,048 / 4,096 / 8,192 / kSliceCap nonzeros (the
+// compact 256-thread class fits two CTAs per SM where the 512-thread one fits
+// one: 47.2 -> 46.5 ms per W half on the large corpus at a steady state; one
+// compact warp per unit up to 2,048 measured slower, 49.8), then a cluster of 2, 3, 4, 6, 8 or
 // 16 such 512-thread CTAs (the smallest whose slices hold kSliceCap), all
 // with the per-nonzero state in shared memory; past that (or where no cluster
 // can be scheduled) one 512-thread CTA per unit with the state in the slot.
@@ -1769,6 +1750,7 @@ const SparseKind kSparseKinds[] = {
     {(const void *)sparse_kernel<32, true, true>, 32, 32, 1024, true, true, 1, 0, "sparse_warp_1k"},
     {(const void *)sparse_kernel<128, true>, 128, 32, 2048, true, false, 1, 0, "sparse_cta128"},
     {(const void *)sparse_kernel<256, true>, 256, 32, 4096, true, false, 1, 0, "sparse_cta256"},
+    {(const void *)sparse_kernel<256, true, true>, 256, 32, 8192, true, true, 1, 0, "sparse_cta256c"},
     {(const void *)sparse_kernel<512, true, true>, 512, 32, kSliceCap, true, true, 1, 0, "sparse_cta512"},
     {(const void *)NMFKL_SPARSE_CLU, 512, 32, 2 * kSliceCap, true, true, 2, 0, "sparse_cluster2"},
     {(const void *)NMFKL_SPARSE_CLU, 512, 32, 3 * kSliceCap, true, true, 3, 0, "sparse_cluster3"},
@@ -1989,7 +1971,6 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
                          "copy unit list"))
                 return NMFKL_ECUDA;
             c->plan_sparse[side].push_back(b);
-            c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
         }
     }
     // in decreasing length, so each class's list comes out longest first; the
@@ -2071,7 +2052,6 @@ nmfkl_status plan_side_sparse(nmfkl_ctx *c, int side, const std::vector<int64_t>
                      "copy unit list"))
             return NMFKL_ECUDA;
         c->plan_sparse[side].push_back(b);
-        c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
     }
     return NMFKL_OK;
 }
@@ -2132,7 +2112,6 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
                          "copy unit list"))
                 return NMFKL_ECUDA;
             c->plan[side].push_back(b);
-            c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
             continue;
         }
         const bool cta = b.nt > 32;
@@ -2179,9 +2158,38 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
                      "copy unit list"))
             return NMFKL_ECUDA;
         c->plan[side].push_back(b);
-        c->scratch_floats = std::max<int64_t>(c->scratch_floats, b.slot_floats * b.groups);
     }
-    return plan_side_sparse(c, side, ptr, order, optin);
+    const nmfkl_status st = plan_side_sparse(c, side, ptr, order, optin);
+    if (st != NMFKL_OK) return st;
+    // Overlapped launches and scratch. A plan with cluster buckets runs its
+    // buckets longest first, each launch allowed to start while the previous
+    // one drains (programmatic dependent launch): the later buckets' blocks
+    // fill the SMs that clusters leave idle and the earlier buckets' tails.
+    // Its buckets may then run at once, so each gets scratch slots of its own
+    // (128-byte aligned offsets). A plan without clusters runs its buckets
+    // one after the other in the table's order and shares one scratch region.
+    // (Measured on the large corpus at a steady state, W half: 48.8 ms in
+    // sequence, 47.0 overlapped longest first, 54.6 overlapped shortest first;
+    // F half, which has no clusters: 40.8 in sequence, 48.0 overlapped: the
+    // concurrent dense-tile buckets contend for L2.) The two plans of a half
+    // never both use their scratch (the one not chosen returns before
+    // touching it), and halves run one after the other, so the buffer is the
+    // largest plan's need.
+    for (int lp = 0; lp < 2; ++lp) {
+        std::vector<Bucket> &plan = lp ? c->plan_sparse[side] : c->plan[side];
+        bool clusters = false;
+        for (const Bucket &b : plan) clusters = clusters || b.cl > 1;
+        c->overlap[side][lp] = c->pdl && clusters;
+        int64_t off = 0, need = 0;
+        for (Bucket &b : plan) {
+            const int64_t fl = (b.slot_floats * b.groups + 31) / 32 * 32;
+            b.scratch_off = c->overlap[side][lp] ? off : 0;
+            off += fl;
+            need = std::max(need, c->overlap[side][lp] ? off : fl);
+        }
+        c->scratch_floats = std::max<int64_t>(c->scratch_floats, need);
+    }
+    return NMFKL_OK;
 }
 
 // The kernel that runs a short length class of the list plan: the chosen one
@@ -2195,27 +2203,34 @@ int short_kernel(const nmfkl_ctx *c, int side, int cls) {
 
 namespace {
 // Launches one bucket of a half on stream st.
-cudaError_t launch_bucket(const Bucket &b, HalfArgs &a, cudaStream_t st) {
+// One bucket's persistent launch. `pdl`: the launch may begin while the
+// previous kernel on the stream is still running (programmatic dependent
+// launch; every bucket kernel waits for its predecessor before it exits).
+cudaError_t launch_bucket(const Bucket &b, HalfArgs &a, cudaStream_t st, bool pdl) {
     void *args[] = {&a};
-    if (b.group) return cudaLaunchKernel(group_kind(b.kind).fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
-    if (b.sparse && b.cl == 1)
-        return cudaLaunchKernel(kSparseKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
+    const void *fn = b.group ? group_kind(b.kind).fn : (b.sparse ? kSparseKinds[b.kind].fn : kKinds[b.kind].fn);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(b.grid);
+    cfg.blockDim = dim3(b.block);
+    cfg.dynamicSmemBytes = b.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
     if (b.cl > 1) {
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(b.grid);
-        cfg.blockDim = dim3(b.block);
-        cfg.dynamicSmemBytes = b.smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = b.cl;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelExC(&cfg, b.sparse ? kSparseKinds[b.kind].fn : kKinds[b.kind].fn, args);
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = b.cl;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
     }
-    return cudaLaunchKernel(kKinds[b.kind].fn, dim3(b.grid), dim3(b.block), args, b.smem, st);
+    if (pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 // The plan of a half from the fixed factor's density at the nonzeros of V
@@ -2236,6 +2251,7 @@ __global__ void plan_select_kernel(const unsigned long long *dens, double denom,
 // not chosen returns at once. With `sweep_dev` set the kernels read the sweep
 // index from it (a captured step), else they take `sweep`.
 nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *sweep_dev, int64_t u0, int64_t u1) {
+    TraceRange trace(side == 0 ? "F half" : "W half");
     const bool F = side == 0;
     const float *At = F ? c->Wt : c->Ft;
     float *X = F ? c->Ft : c->Wt;
@@ -2304,22 +2320,40 @@ nmfkl_status run_half(nmfkl_ctx *c, int side, int64_t sweep, const int64_t *swee
     // concurrently on side streams, so that one bucket's tail overlaps the
     // next one's work, was measured slower: 139 vs 133 ms per step on the
     // large corpus; the concurrent persistent kernels contend for L2.)
+    // Every work queue of the half is reset at once, so that the bucket
+    // launches follow one another directly on the stream; in a plan marked
+    // for overlap (see plan_side) they go longest first and each may start
+    // while the one before drains its tail (not with kernel timing on, where
+    // events separate the launches).
+    if (!cuda_ok(c, cudaMemsetAsync(c->queues + side * kQueuesPerSide, 0, kQueuesPerSide * sizeof(int32_t),
+                                    c->stream),
+                 "reset queues"))
+        return NMFKL_ECUDA;
     int qi = 0;
+    bool first = true;
     for (int lp = 0; lp < 2; ++lp) {
         if (!run_plan[lp]) continue;
         a.plan_id = lp;
-        for (auto &b : lp ? c->plan_sparse[side] : c->plan[side]) {
+        const std::vector<Bucket> &plan = lp ? c->plan_sparse[side] : c->plan[side];
+        const bool overlap = c->overlap[side][lp] && !c->timing;
+        const int nb = (int)plan.size();
+        for (int i = 0; i < nb; ++i) {
+            const Bucket &b = plan[overlap ? nb - 1 - i : i];
             // the alternative of a short length class that was not chosen
             if (b.short_class >= 0 && (b.group ? 1 : 0) != short_kernel(c, side, b.short_class)) continue;
+            if (qi >= kQueuesPerSide) {
+                c->err = "run_half: more buckets than work queues";
+                return NMFKL_EINVAL;
+            }
             a.units = b.d_units;
             a.count = b.count;
             a.queue = c->queues + side * kQueuesPerSide + qi++;
+            a.scratch = c->scratch + b.scratch_off;
             a.slot_floats = b.slot_floats;
             a.lcap = b.lcap;
-            if (!cuda_ok(c, cudaMemsetAsync(a.queue, 0, sizeof(int32_t), c->stream), "reset queue"))
-                return NMFKL_ECUDA;
             const int tok = timer_begin(c, bucket_timer_name(b, side));
-            const cudaError_t e = launch_bucket(b, a, c->stream);
+            const cudaError_t e = launch_bucket(b, a, c->stream, overlap && !first);
+            first = false;
             timer_end(c, tok);
             if (!cuda_ok(c, e, bucket_name(b))) return NMFKL_ECUDA;
         }

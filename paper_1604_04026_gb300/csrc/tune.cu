@@ -154,6 +154,7 @@ nmfkl_status nmfkl_autotune(nmfkl_ctx *c, int64_t sweep, int32_t reps, const cha
         return NMFKL_EINVAL;
     }
     cudaSetDevice(c->device);
+    TraceRange trace("nmfkl autotune");
     if (!cache_path) cache_path = std::getenv("NMFKL_TUNE_CACHE");
     if (from_cache) *from_cache = 0;
     double dens[2];

@@ -125,7 +125,10 @@ def test_full_size_sampled_parity_regularized(large):
     the Uniform start and the W half from the same start (W0, F0), sampled
     columns and rows against the oracle's Algorithm 2 one by one."""
     V = large
-    reg = dict(alpha_W=0.05, beta_W=0.02, alpha_F=0.1, beta_F=0.01)
+    # weights comparable with the linear terms they join: from the Uniform
+    # start sumW_k ~ n / 2 = 50,000 (F half) and sumF_k ~ m / 2 = 500,000
+    # (W half); beta is a tenth of that, alpha x about as much at x ~ 0.5
+    reg = dict(alpha_W=1e5, beta_W=5e4, alpha_F=1e4, beta_F=5e3)
     p = nk.default_params(R, seed=SEED, **reg)
     rng = np.random.default_rng(11)
     W0 = oracle.uniform_init(SEED, 0, R, V.n)

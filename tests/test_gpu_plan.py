@@ -99,3 +99,31 @@ def test_autotune_applies_caches_and_leaves_state(docs, tmp_path):
     m2.set_plan_choice(short_kernel=res["short_kernel"])
     assert m2.step(3) == kl_a
     m2.close()
+
+
+def test_metrics_one_line_per_step(docs, tmp_path):
+    V, r = docs, 12
+    W0, F0 = start(V, r, seed=2)
+    path = str(tmp_path / "metrics.jsonl")
+    m = model(V, W0, F0, params(r, seed=3))
+    m.set_metrics(path)
+    kls = [m.step(s) for s in range(3)]
+    W, F = m.get_W(), m.get_F()
+    m.set_metrics(None)
+    m.step(3)  # not recorded
+    lines = [json.loads(x) for x in open(path).read().splitlines()]
+    assert [x["sweep"] for x in lines] == [0, 1, 2]
+    assert [x["kl"] for x in lines] == kls
+    last = lines[-1]
+    assert last["zeros_W_pct"] == pytest.approx(100.0 * (W == 0).mean(), rel=1e-5, abs=1e-9)
+    assert last["zeros_F_pct"] == pytest.approx(100.0 * (F == 0).mean(), rel=1e-5, abs=1e-9)
+    for x in lines:
+        assert x["ms"] > 0 and x["updates_per_s"] == pytest.approx(2 * V.nnz * r / (x["ms"] / 1e3), rel=1e-4)
+        assert x["evals_per_coord"] >= 1.0 and 0.0 <= x["steps_per_coord"] <= x["evals_per_coord"]
+        assert x["plan"][0] in ("dense", "list") and x["plan"][1] in ("dense", "list")
+    # fit: one line per sweep it ran
+    m.set_metrics(path)
+    trace = m.fit(sweep0=4, max_sweeps=2, rel_tol=0.0)
+    m.close()
+    lines = [json.loads(x) for x in open(path).read().splitlines()]
+    assert [x["sweep"] for x in lines[3:]] == [4, 5]

@@ -135,3 +135,32 @@ def test_admission_limits_and_bad_requests(model):
         assert busy_fit.status == "OK" and tb.status == "EINVAL" and tg.status == "OK"
         F, s, o = _fold_alone(W, p, good, 1e-6, 100)
         assert np.array_equal(tg.F, F)
+
+
+def test_cancel_withdraws_only_queued_requests(model):
+    W, V = model
+    r = W.shape[0]
+    p = params(r, seed=8)
+    with nk.Server(W, params=p, slots=1) as srv:
+        # a long factorization (a second or more) holds the only slot; fold-in
+        # requests wait behind it
+        busy = srv.submit_fit(synth.poisson_lowrank(6000, 6000, 8, density=0.02, seed=1), 16, seed=1,
+                              rel_tol=0.0, max_sweeps=3000)
+        time.sleep(0.1)
+        ts = [srv.submit_foldin(_subset(V, np.arange(10 * i, 10 * i + 10)), rel_tol=1e-6) for i in range(3)]
+        assert srv.cancel(ts[1])          # still queued: withdrawn
+        assert not srv.cancel(busy)       # running: it completes as usual
+        assert srv.stats()["pending"] == 2
+        for t in [busy] + ts:
+            srv.wait(t)
+        assert busy.status == "OK" and ts[0].status == "OK" and ts[2].status == "OK"
+        assert ts[1].status == "ECANCELED" and ts[1].message
+        assert not ts[1].F.any()          # its outputs were never written
+        # the others are what they are alone
+        for i in (0, 2):
+            F, _, _ = _fold_alone(W, p, _subset(V, np.arange(10 * i, 10 * i + 10)), 1e-6, 100)
+            assert np.array_equal(ts[i].F, F)
+        # a collected ticket is unknown
+        with pytest.raises(nk.NMFKLError) as e:
+            srv.cancel(ts[1])
+        assert e.value.status_name == "EINVAL"
