@@ -380,7 +380,9 @@ nmfkl_status nmfkl_debug_perm(nmfkl_ctx *ctx, int64_t sweep, int32_t side, int64
  *   Wt float[n * ldr]: W unit-major (row i holds W[0..r-1, i]), ldr =
  *     4 * ceil(r / 4), padding entries (k >= r) 0;
  *   Ft float[m * ldr]: F unit-major, padding entries 0, read as the start
- *     and overwritten.
+ *     and overwritten;
+ *   Wt and Ft start on a 16-byte boundary (EINVAL otherwise, before any
+ *     launch).
  * These preconditions are not checked: an index out of range reads out of
  * bounds, and nonzero padding or bad values give wrong results or NaN
  * (reported as ENUMERIC).

@@ -2666,6 +2666,8 @@ extern "C" nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, 
     if (!p || p->r < 1 || p->r > kMaxR || n < 1 || m < 1 || n > INT32_MAX || m > INT32_MAX || max_len < 0 ||
         max_len > 256 || !colptr || !Wt || !Ft || (max_len > 0 && (!rowidx || !val)))
         return NMFKL_EINVAL;
+    // the factor rows are read and written 16 bytes at a time
+    if ((reinterpret_cast<uintptr_t>(Wt) | reinterpret_cast<uintptr_t>(Ft)) % 16 != 0) return NMFKL_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return NMFKL_ECUDA;
     unsigned char *base = nullptr;

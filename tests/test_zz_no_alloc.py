@@ -98,6 +98,11 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     big.r = 300
     assert lib.nmfkl_sweep_F_noalloc(ctypes.byref(big), V.n, V.m, 128, *args) == 1
     assert torch.equal(Ft, F_start)
+    # factors off a 16-byte boundary are refused before any launch
+    Wt_off = torch.zeros(Wt.numel() + 1, dtype=torch.float32, device="cuda")
+    bad = (args[0], args[1], args[2], Wt_off.data_ptr() + 4, args[4], 0, None)
+    assert lib.nmfkl_sweep_F_noalloc(ctypes.byref(p), V.n, V.m, 128, *bad) == 1
+    assert torch.equal(Ft, F_start)
     # max_len 32 selects the kernel that holds 32 nonzeros per column; every
     # column here is longer, so each is refused after the launch and left as it was
     assert lib.nmfkl_sweep_F_noalloc(ctypes.byref(p), V.n, V.m, 32, *args) == 1
