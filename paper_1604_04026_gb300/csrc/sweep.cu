@@ -1411,6 +1411,11 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             // no register is copied while its load may be outstanding).
             int2 qa[E], qb[E];
             int ca = 0, cb = 0;
+            // The list two coordinates ahead is prefetched into L2: lists are
+            // written at staging and have left L2 by the time their coordinate
+            // comes, so without it the register prefetch one coordinate ahead
+            // (and the tail beyond it) waits on DRAM. (86.5 -> 83.1 ms per step
+            // on the large corpus at a steady state; 83.5 at four ahead.)
             auto fetch = [&](int pos, int2 (&dst)[E], int &cn) {
                 cn = 0;
                 if (pos < r) {
@@ -1422,6 +1427,13 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                         const int j = glane + CH * t;
                         dst[t] = j < cn ? __ldcg(lk + j) : make_int2(0, 0);
                     }
+                }
+                if (pos + 2 < r) {
+                    const int k2 = perm[pos + 2];
+                    const int c2 = mycnt[k2];
+                    const char *l2 = reinterpret_cast<const char *>(mylists + (int64_t)k2 * LW);
+                    for (int b = glane * 128; b < c2 * 8; b += CH * 128)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(l2 + b));
                 }
             };
             // entries beyond the prefetched ones, four loads in flight per lane
