@@ -1411,6 +1411,10 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             // no register is copied while its load may be outstanding).
             int2 qa[E], qb[E];
             int ca = 0, cb = 0;
+            // Prefetched slots past the list's end hold the dummy entry (index
+            // lcap: state zero, A = 0), so evaluations and updates run over all
+            // E slots without a branch (every load issued at once; the dummy
+            // adds exact zeros and stays zero: 83.1 -> 81.6 ms per step).
             // The list two coordinates ahead is prefetched into L2: lists are
             // written at staging and have left L2 by the time their coordinate
             // comes, so without it the register prefetch one coordinate ahead
@@ -1425,7 +1429,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
 #pragma unroll
                     for (int t = 0; t < E; ++t) {
                         const int j = glane + CH * t;
-                        dst[t] = j < cn ? __ldcg(lk + j) : make_int2(0, 0);
+                        dst[t] = j < cn ? __ldcg(lk + j) : make_int2(lcap, 0);
                     }
                 }
                 if (pos + 2 < r) {
@@ -1466,8 +1470,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                         }
                     };
 #pragma unroll
-                    for (int t = 0; t < E; ++t)
-                        if (glane + CH * t < cn) acc(cur[t].x, __int_as_float(cur[t].y));
+                    for (int t = 0; t < E; ++t) acc(cur[t].x, __int_as_float(cur[t].y));
                     for_rest(lk, cn, acc);
                     return reduce(sg, sh);
                 };
@@ -1490,8 +1493,7 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
                         }
                     };
 #pragma unroll
-                    for (int t = 0; t < E; ++t)
-                        if (glane + CH * t < cn) upd(cur[t].x, __int_as_float(cur[t].y));
+                    for (int t = 0; t < E; ++t) upd(cur[t].x, __int_as_float(cur[t].y));
                     for_rest(lk, cn, upd);
                     // the next evaluation may read these entries from other lanes
                     __syncwarp(gmask);
