@@ -237,19 +237,28 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) swee
         // ---- stage A rows, x_p, and the per-nonzero state
         float xr[K], vr[K], wr[K], qr[K];
         int cr[K];
+        // the K indices and values are loaded first, so that the row gathers
+        // of later rounds do not wait on them
+        int ir[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
+            ir[s] = 0;
+            vr[s] = 0.f;
+            const int pl = 32 * warp_in_group + NT * s + lane;
+            if (s < ks && pl < L) {
+                ir[s] = a.idx[base + pl];
+                vr[s] = a.val[base + pl];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            const float v_l = vr[s];
             xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
             if (s < ks) {
                 const int p0 = 32 * warp_in_group + NT * s;
                 if (p0 < L) {
                     const int pl = p0 + lane;
-                    int idx_l = 0;
-                    float v_l = 0.f;
-                    if (pl < L) {
-                        idx_l = a.idx[base + pl];
-                        v_l = a.val[base + pl];
-                    }
+                    const int idx_l = ir[s];
                     const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
                     if (pl < L) {
                         const float x_l = st.terms == 0 ? 0.f : st.x;
@@ -1337,14 +1346,28 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
         const float4 *x4 = reinterpret_cast<const float4 *>(x_init);
         int4 *cnt4 = reinterpret_cast<int4 *>(mycnt);
         const unsigned lt = lanemask_lt() & gmask;
+        // the index and value of the lane's nonzero in the warp's next chunk
+        // are loaded while the current chunk is staged (its row gather waits
+        // on them otherwise: 81.6 -> 81.1 ms per step)
+        int idx_n = 0;
+        float v_n = 0.f;
+        if (CH * w + glane < L) {
+            idx_n = a.idx[base + CH * w + glane];
+            v_n = a.val[base + CH * w + glane];
+        }
         for (int c = w; c < nchunks; c += kNW) {
             const int p = CH * c + glane;
             const bool valid = p < L;
-            int idx = 0;
-            float v = 0.f;
-            if (valid) {
-                idx = a.idx[base + p];
-                v = a.val[base + p];
+            const int idx = idx_n;
+            const float v = v_n;
+            {
+                const int pn = p + CH * kNW;
+                idx_n = 0;
+                v_n = 0.f;
+                if (pn < L) {
+                    idx_n = a.idx[base + pn];
+                    v_n = a.val[base + pn];
+                }
             }
             const float4 *row = reinterpret_cast<const float4 *>(a.At + (int64_t)idx * ldr);
             float acc = 0.f;
