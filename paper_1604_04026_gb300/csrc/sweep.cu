@@ -124,22 +124,32 @@ __device__ __forceinline__ Staged stage_lane(const HalfArgs &a, float *tile, con
 // Register-resident groups: NT threads (32 = one warp per subproblem, several
 // per block; otherwise one CTA), K nonzeros per thread, so L <= NT*K.
 // ---------------------------------------------------------------------------
-// Minimum resident blocks per SM for the register budget: 64 registers for
-// the warp kernels with K <= 2 (32 warps per SM), 80 for K = 4 (24 warps),
-// 128 for the rest (16 warps). (K = 4 at 64 and K = 8 at 80 registers spill
-// and were measured slower; so was a deeper tile ring: the warp kernels run
-// a 4-deep ring.)
-template <int NT, int K>
-__host__ __device__ constexpr int min_blocks() {
-    return NT == 32 ? (K <= 2 ? 4 : (K == 4 ? 3 : 2)) : (512 / NT > 1 ? 512 / NT : 1);
-}
 // Kernel modes: one half sweep, the allocation-free F half (units are the
 // column indices themselves), and fold-in (each column runs its own sweeps of
 // Algorithm 2 until its objective settles, with the tile staged once).
 constexpr int kModeHalf = 0, kModeFree = 1, kModeFold = 2;
 
+// Block shape of the one-warp-per-unit kernels: threads per block and the
+// minimum resident blocks per SM, which sets the register budget. In a half,
+// K = 4 runs 7-warp blocks four to an SM (28 warps, 72 registers) and K = 8
+// 6-warp blocks three to an SM (18 warps, 112 registers): 81.1 -> 80.8 and
+// -> 80.6 ms per step against 8-warp blocks (24 and 16 warps). Otherwise 8
+// warps per block, 64 registers for K <= 2 (32 warps per SM), 80 for K = 4,
+// 128 for the rest. (K = 4 at 64 and K = 8 at 80 registers with 8-warp blocks
+// spill and were measured slower; so was a deeper tile ring: the warp kernels
+// run a 4-deep ring.) Fold-in and the allocation-free path keep 8-warp blocks.
+__host__ __device__ constexpr int warp_block_threads(int K, int mode) {
+    return mode != kModeHalf ? 256 : (K == 8 ? 192 : (K == 4 ? 224 : 256));
+}
+template <int NT, int K, int kMode = kModeHalf>
+__host__ __device__ constexpr int min_blocks() {
+    return NT == 32 ? (kMode == kModeHalf && K == 8 ? 3 : (K <= 2 || (kMode == kModeHalf && K == 4) ? 4 : (K == 4 ? 3 : 2)))
+                    : (512 / NT > 1 ? 512 / NT : 1);
+}
+
 template <int NT, int K, int D, int kMode = kModeHalf>
-__global__ void __launch_bounds__(NT == 32 ? 256 : NT, min_blocks<NT, K>()) sweep_kernel(HalfArgs a) {
+__global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, min_blocks<NT, K, kMode>())
+    sweep_kernel(HalfArgs a) {
     PdlScope pdl;
     if (plan_skip(a)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2160,7 +2170,7 @@ nmfkl_status plan_side(nmfkl_ctx *c, int side) {
             // warp groups: up to 8 per block; sub-warp groups: whole warps of
             // them, up to 256 threads
             const int step = b.nt < 32 ? 32 / b.nt : 1;
-            groups_per_block = 256 / b.nt;
+            groups_per_block = b.nt == 32 ? warp_block_threads(b.k, kModeHalf) / 32 : 256 / b.nt;
             while (groups_per_block > step && gbytes * groups_per_block > (size_t)optin) groups_per_block -= step;
         }
         b.block = cta ? b.nt : b.nt * groups_per_block;
