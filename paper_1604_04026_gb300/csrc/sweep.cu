@@ -132,18 +132,19 @@ constexpr int kModeHalf = 0, kModeFree = 1, kModeFold = 2;
 // Block shape of the one-warp-per-unit kernels: threads per block and the
 // minimum resident blocks per SM, which sets the register budget. In a half,
 // K = 4 runs 7-warp blocks four to an SM (28 warps, 72 registers) and K = 8
-// 6-warp blocks three to an SM (18 warps, 112 registers): 81.1 -> 80.8 and
-// -> 80.6 ms per step against 8-warp blocks (24 and 16 warps). Otherwise 8
+// 5-warp blocks four to an SM (20 warps, 96 registers): 81.1 -> 80.8 and
+// -> 80.3 ms per step against 8-warp blocks (24 and 16 warps; 6-warp blocks
+// three to an SM for K = 8: 80.6, 7-warp blocks three to an SM: spills). Otherwise 8
 // warps per block, 64 registers for K <= 2 (32 warps per SM), 80 for K = 4,
 // 128 for the rest. (K = 4 at 64 and K = 8 at 80 registers with 8-warp blocks
 // spill and were measured slower; so was a deeper tile ring: the warp kernels
 // run a 4-deep ring.) Fold-in and the allocation-free path keep 8-warp blocks.
 __host__ __device__ constexpr int warp_block_threads(int K, int mode) {
-    return mode != kModeHalf ? 256 : (K == 8 ? 192 : (K == 4 ? 224 : 256));
+    return mode != kModeHalf ? 256 : (K == 8 ? 160 : (K == 4 ? 224 : 256));
 }
 template <int NT, int K, int kMode = kModeHalf>
 __host__ __device__ constexpr int min_blocks() {
-    return NT == 32 ? (kMode == kModeHalf && K == 8 ? 3 : (K <= 2 || (kMode == kModeHalf && K == 4) ? 4 : (K == 4 ? 3 : 2)))
+    return NT == 32 ? (kMode == kModeHalf && K == 8 ? 4 : (K <= 2 || (kMode == kModeHalf && K == 4) ? 4 : (K == 4 ? 3 : 2)))
                     : (512 / NT > 1 ? 512 / NT : 1);
 }
 
