@@ -1930,11 +1930,12 @@ std::vector<int32_t> order_by_length(const std::vector<int64_t> &ptr) {
 // Units of at most this many nonzeros have two alternatives in the list plan,
 // chosen per length class (at most 32, 64, 128, 256 nonzeros): the dense-tile
 // warp kernels of the dense plan, or the sub-warp group kernels over lists of
-// the compressed factor rows. Measured on the large corpus at r = 100 at a
-// steady state (sweep 9, the fixed factor ~13% dense at the nonzeros), ms per
-// F half: dense 2.39 / 4.54 / 7.91 / 10.90, group 2.16 / 6.80 / 12.0 / 16.4
-// (the group kernels' list building, about half their time, issues one
-// scattered store per list entry); the dense kernels are the default.
+// the compressed factor rows. Measured by the autotuner on the large corpus at
+// r = 100 after 25 sweeps, ms per F half: dense 2.3 / 4.6 / 9.3 / 12.3, group
+// 10.4 / 20.8 / 56.1 / 68.9 (the group kernels' list building issues one
+// scattered store per list entry); with Eq. 2 weights that leave the factors
+// 99% zeros the group kernels win every class (the lists are nearly empty).
+// The dense kernels are the default.
 constexpr int64_t kDenseBelow = 256;
 
 // Sparse-list plan of one half: the dense buckets of the units of at most
