@@ -23,6 +23,12 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
+// 16-byte copy of which only the first src_bytes (0..16) are read; the rest of
+// the destination is zero-filled (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16z(void *dst, const void *src, int src_bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -115,13 +121,34 @@ __device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsign
 }
 
 // One lane's share of an evaluation (Eq. Partial) over its staged nonzeros
-// s < ks: (sum_s w_s a_s, sum_s q_s a_s^2) with a_s = ac[s * STRIDE]. For even
-// K the even and odd s are accumulated in the two halves of packed registers
-// and added at the end; the entry after the last (s = ks, when ks is odd)
-// must hold a finite value, its w and q being 0.
-template <int K, int STRIDE>
+// s < ks: (sum_s w_s a_s, sum_s q_s a_s^2) with a_s = ac[s * STRIDE], or, for
+// kPiece (K a multiple of 4), a_s = ac[(s / 4) * STRIDE + s % 4], read as one
+// float4 per piece of four (16-byte aligned). For even K the even and odd s
+// are accumulated in the two halves of packed registers and added at the
+// end; the entry after the last (s = ks, when ks is odd) must hold a finite
+// value, its w and q being 0.
+template <int K, int STRIDE, bool kPiece = false>
 __device__ __forceinline__ float2 lane_sums(const float *ac, const float (&wr)[K], const float (&qr)[K], int ks) {
-    if constexpr (K % 2 == 1) {
+    static_assert(!kPiece || K % 4 == 0, "pieces of four entries");
+    if constexpr (kPiece) {
+        unsigned long long g = 0ull, h = 0ull;  // (+0, +0)
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const int s = 4 * q;
+            if (s < ks) {
+                const float4 v = *reinterpret_cast<const float4 *>(ac + q * STRIDE);
+                const unsigned long long a01 = pack2(v.x, v.y), a23 = pack2(v.z, v.w);
+                g = ffma2(pack2(wr[s], wr[s + 1]), a01, g);
+                h = ffma2(fmul2(pack2(qr[s], qr[s + 1]), a01), a01, h);
+                if (s + 2 < ks) {
+                    g = ffma2(pack2(wr[s + 2], wr[s + 3]), a23, g);
+                    h = ffma2(fmul2(pack2(qr[s + 2], qr[s + 3]), a23), a23, h);
+                }
+            }
+        }
+        const float2 gg = unpack2(g), hh = unpack2(h);
+        return make_float2(gg.x + gg.y, hh.x + hh.y);
+    } else if constexpr (K % 2 == 1) {
         float sg = 0.f, sh = 0.f;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
@@ -147,15 +174,46 @@ __device__ __forceinline__ float2 lane_sums(const float *ac, const float (&wr)[K
     }
 }
 
+// One pair of entries (s, s + 1) of an update, a0 and a1 their A entries.
+template <int K>
+__device__ __forceinline__ void pair_update(int s, float a0, float a1, float (&xr)[K], const float (&vr)[K],
+                                            float (&wr)[K], float (&qr)[K], int (&cr)[K], unsigned long long d2,
+                                            int dc, unsigned long long e2) {
+    const float2 x = unpack2(ffma2(d2, pack2(a0, a1), pack2(xr[s], xr[s + 1])));
+    xr[s] = finish_x(x.x, a0, dc, cr[s]);
+    xr[s + 1] = finish_x(x.y, a1, dc, cr[s + 1]);
+    const float2 t = unpack2(fadd2(pack2(xr[s], xr[s + 1]), e2));
+    const unsigned long long ri = pack2(recip(t.x), recip(t.y));
+    const unsigned long long w2 = fmul2(pack2(vr[s], vr[s + 1]), ri);
+    const float2 w = unpack2(w2), q = unpack2(fmul2(w2, ri));
+    wr[s] = w.x;
+    wr[s + 1] = w.y;
+    qr[s] = q.x;
+    qr[s + 1] = q.y;
+}
+
 // One lane's share of an update (Algorithm 2, "Update Ax"): x_s += d a_s on
 // its staged nonzeros s < ks with the positive-term counts, then w_s and q_s
 // refreshed; the same operations, in the same rounding, as step_x and the
 // scalar refresh. For even K the entry after the last (s = ks, ks odd) is
-// updated too: its a_s is 0 and its state stays 0.
-template <int K, int STRIDE>
+// updated too: its a_s is 0 and its state stays 0. a_s is addressed as in
+// lane_sums.
+template <int K, int STRIDE, bool kPiece = false>
 __device__ __forceinline__ void lane_update(const float *ac, float (&xr)[K], const float (&vr)[K], float (&wr)[K],
                                             float (&qr)[K], int (&cr)[K], int ks, float d, int dc, float eps_div) {
-    if constexpr (K % 2 == 1) {
+    static_assert(!kPiece || K % 4 == 0, "pieces of four entries");
+    if constexpr (kPiece) {
+        const unsigned long long d2 = pack2(d, d), e2 = pack2(eps_div, eps_div);
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const int s = 4 * q;
+            if (s < ks) {
+                const float4 v = *reinterpret_cast<const float4 *>(ac + q * STRIDE);
+                pair_update<K>(s, v.x, v.y, xr, vr, wr, qr, cr, d2, dc, e2);
+                if (s + 2 < ks) pair_update<K>(s + 2, v.z, v.w, xr, vr, wr, qr, cr, d2, dc, e2);
+            }
+        }
+    } else if constexpr (K % 2 == 1) {
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             if (s < ks) {
@@ -169,20 +227,7 @@ __device__ __forceinline__ void lane_update(const float *ac, float (&xr)[K], con
         const unsigned long long d2 = pack2(d, d), e2 = pack2(eps_div, eps_div);
 #pragma unroll
         for (int s = 0; s < K; s += 2) {
-            if (s < ks) {
-                const float a0 = ac[s * STRIDE], a1 = ac[(s + 1) * STRIDE];
-                const float2 x = unpack2(ffma2(d2, pack2(a0, a1), pack2(xr[s], xr[s + 1])));
-                xr[s] = finish_x(x.x, a0, dc, cr[s]);
-                xr[s + 1] = finish_x(x.y, a1, dc, cr[s + 1]);
-                const float2 t = unpack2(fadd2(pack2(xr[s], xr[s + 1]), e2));
-                const unsigned long long ri = pack2(recip(t.x), recip(t.y));
-                const unsigned long long w2 = fmul2(pack2(vr[s], vr[s + 1]), ri);
-                const float2 w = unpack2(w2), q = unpack2(fmul2(w2, ri));
-                wr[s] = w.x;
-                wr[s + 1] = w.y;
-                qr[s] = q.x;
-                qr[s + 1] = q.y;
-            }
+            if (s < ks) pair_update<K>(s, ac[s * STRIDE], ac[(s + 1) * STRIDE], xr, vr, wr, qr, cr, d2, dc, e2);
         }
     }
 }

@@ -120,6 +120,83 @@ __device__ __forceinline__ Staged stage_lane(const HalfArgs &a, float *tile, con
     return Staged{acc, cnt};
 }
 
+// Column of entry s of thread t in a tile row and in a ring slot of the dense
+// kernels. With K a multiple of 4 the layout is piece-major: entries 4q..4q+3
+// of a thread are four adjacent columns, and the pieces of consecutive
+// threads are adjacent (column 4 NT q + 4 t + s % 4), so that a thread moves a
+// piece in one 16-byte access and a warp's pieces form one contiguous 512-byte
+// run. Otherwise entry s of thread t is column NT s + t, its nonzero's position.
+template <int K>
+constexpr bool kPieceLayout = K % 4 == 0;
+template <int NT, int K>
+__host__ __device__ constexpr int tile_col(int t, int s) {
+    return kPieceLayout<K> ? 4 * NT * (s >> 2) + 4 * t + (s & 3) : NT * s + t;
+}
+
+// Stages the four nonzeros of one piece (entries 4q..4q+3 of a piece-major
+// tile; bit j of `valid` set where entry 4q + j has a nonzero, idx[j] its row
+// of A): the four A rows are streamed together, kRowBatch 16-byte pieces of
+// each in flight; x_p and the positive-term count of each entry are formed by
+// the same operations, in the same order, as in stage_lane; the piece of tile
+// row k is written as one float4 at tcol + k * lcap (zeros for entries
+// without a nonzero).
+template <int kRowBatch>
+__device__ __forceinline__ void stage_piece(const HalfArgs &a, float *tcol, const float *x_init, const int *xpos,
+                                            const int (&idx)[4], unsigned valid, Staged (&out)[4]) {
+    const int r = a.r, nf4 = a.ldr >> 2;
+    const int64_t lcap = a.lcap;
+    const float4 *row[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) row[j] = reinterpret_cast<const float4 *>(a.At + (int64_t)idx[j] * a.ldr);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x_init);
+    const int4 *p4 = reinterpret_cast<const int4 *>(xpos);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int cnt[4] = {0, 0, 0, 0};
+    for (int f0 = 0; f0 < nf4; f0 += kRowBatch) {
+        float4 buf[kRowBatch][4];
+#pragma unroll
+        for (int b = 0; b < kRowBatch; ++b)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                buf[b][j] = (((valid >> j) & 1u) && f0 + b < nf4) ? __ldg(row[j] + f0 + b)
+                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < kRowBatch; ++b) {
+            const int f = f0 + b;
+            if (f < nf4) {
+                const float4 xv = x4[f];
+                const int4 pv = p4[f];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 av = buf[b][j];
+                    acc[j] = fmaf(av.x, xv.x, acc[j]);
+                    acc[j] = fmaf(av.y, xv.y, acc[j]);
+                    acc[j] = fmaf(av.z, xv.z, acc[j]);
+                    acc[j] = fmaf(av.w, xv.w, acc[j]);
+                    cnt[j] += (av.x > 0.f ? pv.x : 0) + (av.y > 0.f ? pv.y : 0) + (av.z > 0.f ? pv.z : 0) +
+                              (av.w > 0.f ? pv.w : 0);
+                }
+                if (valid) {
+                    const int k = 4 * f;
+                    float4 *dst = reinterpret_cast<float4 *>(tcol + (int64_t)k * lcap);
+                    dst[0] = make_float4(buf[b][0].x, buf[b][1].x, buf[b][2].x, buf[b][3].x);
+                    if (k + 1 < r)
+                        *reinterpret_cast<float4 *>(tcol + (int64_t)(k + 1) * lcap) =
+                            make_float4(buf[b][0].y, buf[b][1].y, buf[b][2].y, buf[b][3].y);
+                    if (k + 2 < r)
+                        *reinterpret_cast<float4 *>(tcol + (int64_t)(k + 2) * lcap) =
+                            make_float4(buf[b][0].z, buf[b][1].z, buf[b][2].z, buf[b][3].z);
+                    if (k + 3 < r)
+                        *reinterpret_cast<float4 *>(tcol + (int64_t)(k + 3) * lcap) =
+                            make_float4(buf[b][0].w, buf[b][1].w, buf[b][2].w, buf[b][3].w);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = Staged{acc[j], cnt[j]};
+}
+
 // ---------------------------------------------------------------------------
 // Register-resident groups: NT threads (32 = one warp per subproblem, several
 // per block; otherwise one CTA), K nonzeros per thread, so L <= NT*K.
@@ -172,7 +249,10 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
     float *x_out = x_init + ldr;
     uint64_t *words = reinterpret_cast<uint64_t *>(gs + lay.aux_off);
     int *xpos = reinterpret_cast<int *>(gs + lay.xpos_off);
-    float *myring = reinterpret_cast<float *>(gs + lay.ring_off) + tid_g;  // slot d, item s at [(d*K + s)*NT]
+    // ring slot d holds entry s of this thread at [d*K*NT + tile_col(tid_g, s)]
+    constexpr bool kPiece = kPieceLayout<K>;
+    constexpr int kRingStride = kPiece ? 4 * NT : NT;  // between pieces (kPiece) or entries
+    float *myring = reinterpret_cast<float *>(gs + lay.ring_off) + tile_col<NT, K>(tid_g, 0);
     float2 *red = reinterpret_cast<float2 *>(gs + lay.red_off);
     __shared__ int s_q;
 
@@ -237,6 +317,8 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
         // ring entries filled per coordinate: for even K a whole number of
         // pairs (the extra entry is zero-filled: its nonzeros lie past L)
         const int ks2 = K % 2 == 0 ? ks + (ks & 1) : ks;
+        // entries of this thread with a nonzero: s < nvalid (nonzero NT s + tid_g < L)
+        const int nvalid = tid_g < L ? (L - tid_g + NT - 1) / NT : 0;
 
         for (int k = tid_g; k < ldr; k += NT) {
             const float xv = a.X[u * ldr + k];
@@ -248,37 +330,97 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
         // ---- stage A rows, x_p, and the per-nonzero state
         float xr[K], vr[K], wr[K], qr[K];
         int cr[K];
-        // the K indices and values are loaded first, so that the row gathers
-        // of later rounds do not wait on them
-        int ir[K];
+        if constexpr (kPiece) {
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
-            ir[s] = 0;
-            vr[s] = 0.f;
-            const int pl = 32 * warp_in_group + NT * s + lane;
-            if (s < ks && pl < L) {
-                ir[s] = a.idx[base + pl];
-                vr[s] = a.val[base + pl];
+            for (int s = 0; s < K; ++s) {
+                xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
             }
-        }
+            // the four indices and values of a piece are loaded one piece
+            // ahead, before the rows of the current piece are streamed
+            int id4[4];
+            float v4[4];
+            auto load_piece = [&](int q, int (&ids)[4], float (&vs)[4]) {
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
-            const float v_l = vr[s];
-            xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
-            if (s < ks) {
-                const int p0 = 32 * warp_in_group + NT * s;
-                if (p0 < L) {
-                    const int pl = p0 + lane;
-                    const int idx_l = ir[s];
-                    const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
+                for (int j = 0; j < 4; ++j) {
+                    const int pl = 32 * warp_in_group + NT * (4 * q + j) + lane;
+                    ids[j] = 0;
+                    vs[j] = 0.f;
                     if (pl < L) {
-                        const float x_l = st.terms == 0 ? 0.f : st.x;
-                        xr[s] = x_l;
-                        cr[s] = st.terms;
-                        vr[s] = v_l;
-                        const float ri = recip(x_l + eps_div);
-                        wr[s] = v_l * ri;
-                        qr[s] = wr[s] * ri;
+                        ids[j] = a.idx[base + pl];
+                        vs[j] = a.val[base + pl];
+                    }
+                }
+            };
+            load_piece(0, id4, v4);
+#pragma unroll
+            for (int q = 0; q < K / 4; ++q) {
+                const int p0 = 32 * warp_in_group + NT * 4 * q;
+                if (p0 < L) {
+                    int idn[4];
+                    float vn[4];
+                    if (q + 1 < K / 4) load_piece(q + 1, idn, vn);
+                    unsigned valid = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (p0 + NT * j + lane < L) valid |= 1u << j;
+                    Staged st[4];
+                    stage_piece<1>(a, tile + tile_col<NT, K>(tid_g, 4 * q), x_init, xpos, id4, valid,
+                                                   st);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if ((valid >> j) & 1u) {
+                            const int s = 4 * q + j;
+                            const float x_l = st[j].terms == 0 ? 0.f : st[j].x;
+                            xr[s] = x_l;
+                            cr[s] = st[j].terms;
+                            vr[s] = v4[j];
+                            const float ri = recip(x_l + eps_div);
+                            wr[s] = v4[j] * ri;
+                            qr[s] = wr[s] * ri;
+                        }
+                    }
+                    if (q + 1 < K / 4) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            id4[j] = idn[j];
+                            v4[j] = vn[j];
+                        }
+                    }
+                }
+            }
+        } else {
+            // the K indices and values are loaded first, so that the row gathers
+            // of later rounds do not wait on them
+            int ir[K];
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                ir[s] = 0;
+                vr[s] = 0.f;
+                const int pl = 32 * warp_in_group + NT * s + lane;
+                if (s < ks && pl < L) {
+                    ir[s] = a.idx[base + pl];
+                    vr[s] = a.val[base + pl];
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                const float v_l = vr[s];
+                xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
+                if (s < ks) {
+                    const int p0 = 32 * warp_in_group + NT * s;
+                    if (p0 < L) {
+                        const int pl = p0 + lane;
+                        const int idx_l = ir[s];
+                        const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
+                        if (pl < L) {
+                            const float x_l = st.terms == 0 ? 0.f : st.x;
+                            xr[s] = x_l;
+                            cr[s] = st.terms;
+                            vr[s] = v_l;
+                            const float ri = recip(x_l + eps_div);
+                            wr[s] = v_l * ri;
+                            qr[s] = wr[s] * ri;
+                        }
                     }
                 }
             }
@@ -298,11 +440,20 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
             // reads them), so the column is in shared memory when its turn comes.
             auto issue = [&](int pos) {
                 if (pos < r) {
-                    const float *col = tile + (int64_t)perm[pos] * lcap + tid_g;
+                    const float *col = tile + (int64_t)perm[pos] * lcap + tile_col<NT, K>(tid_g, 0);
                     float *dst = myring + (pos % D) * K * NT;
+                    if constexpr (kPiece) {
+                        // whole pieces, the entries without a nonzero zero-filled
 #pragma unroll
-                    for (int s = 0; s < K; ++s)
-                        if (s < ks2) cp_async4(dst + s * NT, col + NT * s, tid_g + NT * s < L ? 4 : 0);
+                        for (int q = 0; q < K / 4; ++q)
+                            if (4 * q < ks2)
+                                cp_async16z(dst + q * kRingStride, col + q * kRingStride,
+                                            4 * min(max(nvalid - 4 * q, 0), 4));
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < K; ++s)
+                            if (s < ks2) cp_async4(dst + s * NT, col + NT * s, s < nvalid ? 4 : 0);
+                    }
                 }
                 cp_async_commit();
             };
@@ -337,10 +488,12 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
                 const float *ac = myring + (kk % D) * K * NT;
                 const int k = perm[kk];
                 auto eval = [&]() -> float2 {
-                    const float2 t = lane_sums<K, NT>(ac, wr, qr, ks);
+                    const float2 t = lane_sums<K, kRingStride, kPiece>(ac, wr, qr, ks);
                     return reduce(t.x, t.y);
                 };
-                auto update = [&](float d, int dc) { lane_update<K, NT>(ac, xr, vr, wr, qr, cr, ks, d, dc, eps_div); };
+                auto update = [&](float d, int dc) {
+                    lane_update<K, kRingStride, kPiece>(ac, xr, vr, wr, qr, cr, ks, d, dc, eps_div);
+                };
                 const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
                 if (tid_g == 0) x_out[k] = xk;
             }
@@ -371,7 +524,7 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
                     if (s < ks) {
                         const int p = tid_g + NT * s;
                         if (p < L) {
-                            const float *col = tile + p;
+                            const float *col = tile + tile_col<NT, K>(tid_g, s);
                             float acc = 0.f;
                             int cnt = 0;
 #pragma unroll 4
@@ -424,7 +577,8 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
             }
         }
         group_sync();
-        discard_tile(tile, r, L, lcap, tid_g, NT);
+        // the columns in use: the first L, or the first ceil(ks/4) pieces
+        discard_tile(tile, r, kPiece ? min(lcap, (ks + 3) / 4 * 4 * NT) : L, lcap, tid_g, NT);
         for (int k = tid_g; k < r; k += NT) {
             const float xv = x_out[k];
             if (!(xv == xv)) atomicOr(a.err, kErrNaN);
@@ -471,7 +625,10 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
     float *x_out = x_init + ldr;
     uint64_t *words = reinterpret_cast<uint64_t *>(gs + lay.aux_off);
     int *xpos = reinterpret_cast<int *>(gs + lay.xpos_off);
-    float *myring = reinterpret_cast<float *>(gs + lay.ring_off) + glane;  // slot d, item s at [(d*K + s)*G]
+    // ring slot d holds entry s of this lane at [d*K*G + tile_col(glane, s)]
+    constexpr bool kPiece = kPieceLayout<K>;
+    constexpr int kRingStride = kPiece ? 4 * G : G;
+    float *myring = reinterpret_cast<float *>(gs + lay.ring_off) + tile_col<G, K>(glane, 0);
 
     float *tile = a.scratch + (int64_t)group_global * a.slot_floats;
     const int lcap = a.lcap;
@@ -508,6 +665,7 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
         }
         const int ks = work ? (L + G - 1) / G : 0;
         const int ks2 = K % 2 == 0 ? ks + (ks & 1) : ks;  // whole pairs, the extra entry zero-filled
+        const int nvalid = glane < L ? (L - glane + G - 1) / G : 0;  // entries with a nonzero (L is 0 without work)
         if (work) {
             for (int k = glane; k < ldr; k += G) {
                 const float xv = a.X[u * ldr + k];
@@ -520,26 +678,67 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
         // ---- stage A rows, x_p, and the per-nonzero state (nonzero p = G s + glane)
         float xr[K], vr[K], wr[K], qr[K];
         int cr[K];
+        if constexpr (kPiece) {
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
-            xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
-            if (s < ks) {
-                const int pl = G * s + glane;
-                int idx_l = 0;
-                float v_l = 0.f;
-                if (pl < L) {
-                    idx_l = a.idx[base + pl];
-                    v_l = a.val[base + pl];
+            for (int s = 0; s < K; ++s) {
+                xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
+            }
+#pragma unroll
+            for (int q = 0; q < K / 4; ++q) {
+                if (4 * q < ks) {
+                    unsigned valid = 0;
+                    int id4[4];
+                    float v4[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int pl = G * (4 * q + j) + glane;
+                        id4[j] = 0;
+                        v4[j] = 0.f;
+                        if (pl < L) {
+                            id4[j] = a.idx[base + pl];
+                            v4[j] = a.val[base + pl];
+                            valid |= 1u << j;
+                        }
+                    }
+                    Staged st[4];
+                    stage_piece<1>(a, tile + tile_col<G, K>(glane, 4 * q), x_init, xpos, id4, valid, st);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if ((valid >> j) & 1u) {
+                            const int s = 4 * q + j;
+                            const float x_l = st[j].terms == 0 ? 0.f : st[j].x;
+                            xr[s] = x_l;
+                            cr[s] = st[j].terms;
+                            vr[s] = v4[j];
+                            const float ri = recip(x_l + eps_div);
+                            wr[s] = v4[j] * ri;
+                            qr[s] = wr[s] * ri;
+                        }
+                    }
                 }
-                const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
-                if (pl < L) {
-                    const float x_l = st.terms == 0 ? 0.f : st.x;
-                    xr[s] = x_l;
-                    cr[s] = st.terms;
-                    vr[s] = v_l;
-                    const float ri = recip(x_l + eps_div);
-                    wr[s] = v_l * ri;
-                    qr[s] = wr[s] * ri;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                xr[s] = 0.f; vr[s] = 0.f; wr[s] = 0.f; qr[s] = 0.f; cr[s] = 0;
+                if (s < ks) {
+                    const int pl = G * s + glane;
+                    int idx_l = 0;
+                    float v_l = 0.f;
+                    if (pl < L) {
+                        idx_l = a.idx[base + pl];
+                        v_l = a.val[base + pl];
+                    }
+                    const Staged st = stage_lane(a, tile, x_init, xpos, pl, pl < L, idx_l);
+                    if (pl < L) {
+                        const float x_l = st.terms == 0 ? 0.f : st.x;
+                        xr[s] = x_l;
+                        cr[s] = st.terms;
+                        vr[s] = v_l;
+                        const float ri = recip(x_l + eps_div);
+                        wr[s] = v_l * ri;
+                        qr[s] = wr[s] * ri;
+                    }
                 }
             }
         }
@@ -554,11 +753,19 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
         // ---- Algorithm 2 over the units' coordinates, in step
         auto issue = [&](int pos) {
             if (work && pos < r) {
-                const float *col = tile + (int64_t)perm[pos] * lcap + glane;
+                const float *col = tile + (int64_t)perm[pos] * lcap + tile_col<G, K>(glane, 0);
                 float *dst = myring + (pos % D) * K * G;
+                if constexpr (kPiece) {
 #pragma unroll
-                for (int s = 0; s < K; ++s)
-                    if (s < ks2) cp_async4(dst + s * G, col + G * s, glane + G * s < L ? 4 : 0);
+                    for (int q = 0; q < K / 4; ++q)
+                        if (4 * q < ks2)
+                            cp_async16z(dst + q * kRingStride, col + q * kRingStride,
+                                        4 * min(max(nvalid - 4 * q, 0), 4));
+                } else {
+#pragma unroll
+                    for (int s = 0; s < K; ++s)
+                        if (s < ks2) cp_async4(dst + s * G, col + G * s, s < nvalid ? 4 : 0);
+                }
             }
             cp_async_commit();
         };
@@ -571,7 +778,7 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
                 const float *ac = myring + (kk % D) * K * G;
                 const int k = perm[kk];
                 auto eval = [&]() -> float2 {
-                    const float2 t = lane_sums<K, G>(ac, wr, qr, ks);
+                    const float2 t = lane_sums<K, kRingStride, kPiece>(ac, wr, qr, ks);
                     float sg = t.x, sh = t.y;
 #pragma unroll
                     for (int o = G / 2; o > 0; o >>= 1) {
@@ -580,7 +787,9 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
                     }
                     return make_float2(sg, sh);
                 };
-                auto update = [&](float d, int dc) { lane_update<K, G>(ac, xr, vr, wr, qr, cr, ks, d, dc, eps_div); };
+                auto update = [&](float d, int dc) {
+                    lane_update<K, kRingStride, kPiece>(ac, xr, vr, wr, qr, cr, ks, d, dc, eps_div);
+                };
                 const float xk = newton_coordinate(a, x_init[k], a.sumA[k], eval, update, tally);
                 if (glane == 0) x_out[k] = xk;
             }
@@ -599,7 +808,7 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
                 if (glane == 0) a.unit_obj[u] = dt;
             }
             __syncwarp(gmask);
-            discard_tile(tile, r, L, lcap, glane, G);
+            discard_tile(tile, r, kPiece ? min(lcap, (ks + 3) / 4 * 4 * G) : L, lcap, glane, G);
             for (int k = glane; k < r; k += G) {
                 const float xv = x_out[k];
                 if (!(xv == xv)) atomicOr(a.err, kErrNaN);
