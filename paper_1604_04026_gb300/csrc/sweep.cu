@@ -121,13 +121,18 @@ __device__ __forceinline__ Staged stage_lane(const HalfArgs &a, float *tile, con
 }
 
 // Column of entry s of thread t in a tile row and in a ring slot of the dense
-// kernels. With K a multiple of 4 the layout is piece-major: entries 4q..4q+3
-// of a thread are four adjacent columns, and the pieces of consecutive
-// threads are adjacent (column 4 NT q + 4 t + s % 4), so that a thread moves a
-// piece in one 16-byte access and a warp's pieces form one contiguous 512-byte
-// run. Otherwise entry s of thread t is column NT s + t, its nonzero's position.
+// kernels. With K = 4 or 8 the layout is piece-major: entries 4q..4q+3 of a
+// thread are four adjacent columns, and the pieces of consecutive threads are
+// adjacent (column 4 NT q + 4 t + s % 4), so that a thread moves a piece in
+// one 16-byte access and a warp's pieces form one contiguous 512-byte run.
+// A unit's last piece, when partial, is written whole, zeros standing for
+// the entries without a nonzero, so its tile spans up to 4 NT - 1 columns
+// more than its L nonzeros (more L2 footprint; writing that piece in the
+// nonzeros' own order instead measured slower). Otherwise (and for K = 16,
+// whose four-row staging would not fit the register budget) entry s of
+// thread t is column NT s + t, its nonzero's position.
 template <int K>
-constexpr bool kPieceLayout = K % 4 == 0;
+constexpr bool kPieceLayout = K % 4 == 0 && K <= 8;
 template <int NT, int K>
 __host__ __device__ constexpr int tile_col(int t, int s) {
     return kPieceLayout<K> ? 4 * NT * (s >> 2) + 4 * t + (s & 3) : NT * s + t;
