@@ -38,10 +38,18 @@ __device__ __forceinline__ void cp_async_wait() {
 // Fisher-Yates over {0..r-1} from the identity: step t (i = r-1-t) uses
 // word t, j = floor(word * (i+1) / 2^64).
 __device__ __forceinline__ void fisher_yates(uint8_t *perm, const uint64_t *words, int r) {
-    for (int i = 0; i < r; ++i) perm[i] = (uint8_t)i;
+    // the identity, four entries per 32-bit store (perm is 4-byte aligned and
+    // holds r rounded up to a multiple of 4 bytes)
+    for (int i = 0; i < r; i += 4) *reinterpret_cast<uint32_t *>(perm + i) = 0x03020100u + 0x01010101u * (uint32_t)i;
     int t = 0;
     for (int i = r - 1; i >= 1; --i, ++t) {
-        const int j = (int)__umul64hi(words[t], (uint64_t)(i + 1));
+        // j = floor(words[t] (i + 1) / 2^64) from the 32-bit halves of the word
+        // (i + 1 < 2^32): the low half's product only carries its high half
+        // into the sum, and the sum stays below 2^64
+        const uint64_t w = words[t];
+        const uint32_t n = (uint32_t)(i + 1);
+        const uint64_t hi = (uint64_t)(uint32_t)(w >> 32) * n + __umulhi((uint32_t)w, n);
+        const int j = (int)(hi >> 32);
         const uint8_t tmp = perm[i];
         perm[i] = perm[j];
         perm[j] = tmp;

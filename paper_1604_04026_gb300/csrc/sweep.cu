@@ -463,10 +463,13 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
                 cp_async_commit();
             };
             auto reduce = [&](float sg, float sh) -> float2 {
+                // butterfly over the warp, both sums added by one packed instruction
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    sg += __shfl_xor_sync(kFull, sg, o);
-                    sh += __shfl_xor_sync(kFull, sh, o);
+                    const float ga = __shfl_xor_sync(kFull, sg, o), ha = __shfl_xor_sync(kFull, sh, o);
+                    const float2 t = unpack2(fadd2(pack2(sg, sh), pack2(ga, ha)));
+                    sg = t.x;
+                    sh = t.y;
                 }
                 if constexpr (kCta) {
                     float4 *rb = red4 + parity * kNW;
@@ -787,8 +790,10 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
                     float sg = t.x, sh = t.y;
 #pragma unroll
                     for (int o = G / 2; o > 0; o >>= 1) {
-                        sg += __shfl_xor_sync(gmask, sg, o);
-                        sh += __shfl_xor_sync(gmask, sh, o);
+                        const float ga = __shfl_xor_sync(gmask, sg, o), ha = __shfl_xor_sync(gmask, sh, o);
+                        const float2 u = unpack2(fadd2(pack2(sg, sh), pack2(ga, ha)));
+                        sg = u.x;
+                        sh = u.y;
                     }
                     return make_float2(sg, sh);
                 };
@@ -1471,8 +1476,10 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
     auto reduce = [&](float sg, float sh) -> float2 {
 #pragma unroll
         for (int o = CH / 2; o > 0; o >>= 1) {
-            sg += __shfl_xor_sync(gmask, sg, o);
-            sh += __shfl_xor_sync(gmask, sh, o);
+            const float ga = __shfl_xor_sync(gmask, sg, o), ha = __shfl_xor_sync(gmask, sh, o);
+            const float2 u = unpack2(fadd2(pack2(sg, sh), pack2(ga, ha)));
+            sg = u.x;
+            sh = u.y;
         }
         if constexpr (kCluster) {
             float2 *rb = red + parity * kNW;
@@ -3032,7 +3039,7 @@ extern "C" nmfkl_status nmfkl_sweep_F_noalloc(const nmfkl_params *p, int64_t n, 
 __global__ void debug_perm_kernel(const int64_t *cols, int64_t count, int r, int64_t sweep, int side,
                                   int perm_mode, uint64_t seed, int32_t *out) {
     __shared__ uint64_t words[8][kMaxR];
-    __shared__ uint8_t perm[8][kMaxR];
+    __shared__ __align__(16) uint8_t perm[8][kMaxR];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * 8 + w;
     if (c >= count) return;
