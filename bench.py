@@ -183,7 +183,7 @@ def measured_peak_hbm():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cu", "common.cuh"):
+    for f in ("sweep.cu", "common.cuh", "device_util.cuh"):
         with open(os.path.join(ROOT, "paper_1604_04026_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -127,6 +127,10 @@ __device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsign
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+// (a.x + b.x, a.y + b.y) in one packed instruction
+__device__ __forceinline__ float2 add_pair(float2 a, float2 b) {
+    return unpack2(fadd2(pack2(a.x, a.y), pack2(b.x, b.y)));
+}
 
 // One lane's share of an evaluation (Eq. Partial) over its staged nonzeros
 // s < ks: (sum_s w_s a_s, sum_s q_s a_s^2) with a_s = ac[s * STRIDE], or, for

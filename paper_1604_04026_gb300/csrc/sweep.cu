@@ -475,15 +475,14 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
                     float4 *rb = red4 + parity * kNW;
                     if (lane == 0) rb[warp_in_block] = make_float4(sg, sh, 0.f, 0.f);
                     __syncthreads();
-                    float tg = 0.f, th = 0.f;
+                    float2 t = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int w = 0; w < kNW; ++w) {
                         const float4 v = rb[w];
-                        tg += v.x;
-                        th += v.y;
+                        t = add_pair(t, make_float2(v.x, v.y));
                     }
                     parity ^= 1;
-                    return make_float2(tg, th);
+                    return t;
                 } else {
                     return make_float2(sg, sh);
                 }
@@ -1486,37 +1485,25 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
             __syncthreads();
             parity ^= 1;
-            float cg = 0.f, ch = 0.f;
+            float2 c = make_float2(0.f, 0.f);
             if (warp_in_block == 0) {
 #pragma unroll
-                for (int i = 0; i < kNW; ++i) {
-                    const float2 v = rb[i];
-                    cg += v.x;
-                    ch += v.y;
-                }
+                for (int i = 0; i < kNW; ++i) c = add_pair(c, rb[i]);
             }
             float2 tot = make_float2(0.f, 0.f);
-            cluster_sum(pack_f2(cg, ch), [&](const unsigned long long *sl, int n) {
-                for (int i = 0; i < n; ++i) {
-                    const float2 v = unpack_f2(sl[i]);
-                    tot.x += v.x;
-                    tot.y += v.y;
-                }
+            cluster_sum(pack_f2(c.x, c.y), [&](const unsigned long long *sl, int n) {
+                for (int i = 0; i < n; ++i) tot = add_pair(tot, unpack_f2(sl[i]));
             });
             return tot;
         } else if constexpr (kCta) {
             float2 *rb = red + parity * kNW;
             if (lane == 0) rb[warp_in_block] = make_float2(sg, sh);
             __syncthreads();
-            float tg = 0.f, th = 0.f;
+            float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < kNW; ++i) {
-                const float2 v = rb[i];
-                tg += v.x;
-                th += v.y;
-            }
+            for (int i = 0; i < kNW; ++i) t = add_pair(t, rb[i]);
             parity ^= 1;
-            return make_float2(tg, th);
+            return t;
         } else {
             return make_float2(sg, sh);
         }
