@@ -35,29 +35,34 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Fisher-Yates over {0..r-1} from the identity: step t (i = r-1-t) uses
-// word t, j = floor(word * (i+1) / 2^64).
-__device__ __forceinline__ void fisher_yates(uint8_t *perm, const uint64_t *words, int r) {
+// Swap index of Fisher-Yates step t over {0..r-1} (position i = r-1-t, n =
+// i + 1 = r - t): j = floor(w n / 2^64) for the step's Philox word w, formed
+// from the word's 32-bit halves (n < 2^32): the low half's product only
+// carries its high half into the sum, and the sum stays below 2^64.
+__device__ __forceinline__ int swap_index(uint64_t w, uint32_t n) {
+    const uint64_t hi = (uint64_t)(uint32_t)(w >> 32) * n + __umulhi((uint32_t)w, n);
+    return (int)(hi >> 32);
+}
+
+// Fisher-Yates over {0..r-1} from the identity: step t swaps position
+// i = r-1-t with swaps[t] (from ids_swaps_warp).
+__device__ __forceinline__ void fisher_yates(uint8_t *perm, const uint8_t *swaps, int r) {
     // the identity, four entries per 32-bit store (perm is 4-byte aligned and
     // holds r rounded up to a multiple of 4 bytes)
     for (int i = 0; i < r; i += 4) *reinterpret_cast<uint32_t *>(perm + i) = 0x03020100u + 0x01010101u * (uint32_t)i;
     int t = 0;
     for (int i = r - 1; i >= 1; --i, ++t) {
-        // j = floor(words[t] (i + 1) / 2^64) from the 32-bit halves of the word
-        // (i + 1 < 2^32): the low half's product only carries its high half
-        // into the sum, and the sum stays below 2^64
-        const uint64_t w = words[t];
-        const uint32_t n = (uint32_t)(i + 1);
-        const uint64_t hi = (uint64_t)(uint32_t)(w >> 32) * n + __umulhi((uint32_t)w, n);
-        const int j = (int)(hi >> 32);
+        const int j = swaps[t];
         const uint8_t tmp = perm[i];
         perm[i] = perm[j];
         perm[j] = tmp;
     }
 }
 
-// The r-1 Philox words of a unit's order, generated by `nlanes` lanes.
-__device__ __forceinline__ void ids_words_warp(uint64_t *words, int r, int64_t unit, int64_t sweep,
+// The r-1 swap indices of a unit's order, one byte each (r <= 256), from its
+// r-1 Philox words, generated by `nlanes` lanes in parallel, so that the
+// sequential shuffle (one lane) only moves entries.
+__device__ __forceinline__ void ids_swaps_warp(uint8_t *swaps, int r, int64_t unit, int64_t sweep,
                                                int side, int perm_mode, uint64_t seed, int lane,
                                                int nlanes = 32) {
     const int nw = r - 1;
@@ -67,8 +72,10 @@ __device__ __forceinline__ void ids_words_warp(uint64_t *words, int r, int64_t u
         ids_counter(c, (uint64_t)b, unit, sweep, side, perm_mode);
         philox4x64_10(c, seed, kKeyIds);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (4 * b + j < nw) words[4 * b + j] = c[j];
+        for (int j = 0; j < 4; ++j) {
+            const int t = 4 * b + j;
+            if (t < nw) swaps[t] = (uint8_t)swap_index(c[j], (uint32_t)(r - t));
+        }
     }
 }
 

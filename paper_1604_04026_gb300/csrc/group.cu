@@ -204,9 +204,9 @@ __global__ void __launch_bounds__(256) group_kernel(HalfArgs a) {
                 const int64_t perm_unit = a.unit_ids ? a.unit_ids[u] : u;
                 // ---- the unit's coordinates and its order of Algorithm 1's ids
                 for (int k = glane; k < ldr; k += G) x[k] = a.X[u * ldr + k];
-                ids_words_warp(words, r, perm_unit, sweep_of(a), a.side, a.perm_mode, a.seed, glane, G);
+                ids_swaps_warp(reinterpret_cast<uint8_t *>(words), r, perm_unit, sweep_of(a), a.side, a.perm_mode, a.seed, glane, G);
                 __syncwarp(gmask);
-                if (glane == 0) fisher_yates(perm, words, r);
+                if (glane == 0) fisher_yates(perm, reinterpret_cast<const uint8_t *>(words), r);
                 __syncwarp(gmask);
                 // the words are consumed: the region now holds the counts and the state
                 for (int i = glane; i < (r * G) / 4; i += G) reinterpret_cast<uint32_t *>(cnt)[i] = 0u;

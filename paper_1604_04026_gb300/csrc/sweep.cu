@@ -434,9 +434,9 @@ __global__ void __launch_bounds__(NT == 32 ? warp_block_threads(K, kMode) : NT, 
         // ---- one pass of Algorithm 2 over the unit's coordinates (order of `sweep`)
         auto run_coordinates = [&](int64_t sweep) {
             if (warp_in_group == 0) {
-                ids_words_warp(words, r, perm_unit, sweep, a.side, a.perm_mode, a.seed, lane);
+                ids_swaps_warp(reinterpret_cast<uint8_t *>(words), r, perm_unit, sweep, a.side, a.perm_mode, a.seed, lane);
                 __syncwarp();
-                if (lane == 0) fisher_yates(perm, words, r);
+                if (lane == 0) fisher_yates(perm, reinterpret_cast<const uint8_t *>(words), r);
                 __syncwarp();
             }
             group_sync();
@@ -751,9 +751,9 @@ __global__ void __launch_bounds__(256, sub_min_blocks<G, K>()) sweep_sub_kernel(
         }
         if (work) {
             const int64_t perm_unit = a.unit_ids ? a.unit_ids[u] : u;
-            ids_words_warp(words, r, perm_unit, sweep, a.side, a.perm_mode, a.seed, glane, G);
+            ids_swaps_warp(reinterpret_cast<uint8_t *>(words), r, perm_unit, sweep, a.side, a.perm_mode, a.seed, glane, G);
             __syncwarp(gmask);
-            if (glane == 0) fisher_yates(perm, words, r);
+            if (glane == 0) fisher_yates(perm, reinterpret_cast<const uint8_t *>(words), r);
         }
         __syncwarp();
 
@@ -898,9 +898,9 @@ __global__ void __launch_bounds__(kGiantNT) sweep_giant_kernel(HalfArgs a) {
             }
         }
         if (warp == 0) {
-            ids_words_warp(words, r, u, sweep_of(a), a.side, a.perm_mode, a.seed, lane);
+            ids_swaps_warp(reinterpret_cast<uint8_t *>(words), r, u, sweep_of(a), a.side, a.perm_mode, a.seed, lane);
             __syncwarp();
-            if (lane == 0) fisher_yates(perm, words, r);
+            if (lane == 0) fisher_yates(perm, reinterpret_cast<const uint8_t *>(words), r);
             __syncwarp();
         }
         __syncthreads();
@@ -1149,9 +1149,9 @@ __global__ void __launch_bounds__(NT, 1) sweep_cluster_kernel(HalfArgs a) {
             }
         }
         if (warp == 0) {
-            ids_words_warp(words, r, u, sweep_of(a), a.side, a.perm_mode, a.seed, lane);
+            ids_swaps_warp(reinterpret_cast<uint8_t *>(words), r, u, sweep_of(a), a.side, a.perm_mode, a.seed, lane);
             __syncwarp();
-            if (lane == 0) fisher_yates(perm, words, r);
+            if (lane == 0) fisher_yates(perm, reinterpret_cast<const uint8_t *>(words), r);
             __syncwarp();
         }
         __syncthreads();
@@ -1638,9 +1638,9 @@ __global__ void __launch_bounds__(NT == 32 ? 256 : NT, (sparse_min_blocks<NT, kS
             __syncwarp(gmask);
         }
         if (w == 0) {
-            ids_words_warp(words, r, perm_unit, sweep_of(a), a.side, a.perm_mode, a.seed, glane, CH);
+            ids_swaps_warp(reinterpret_cast<uint8_t *>(words), r, perm_unit, sweep_of(a), a.side, a.perm_mode, a.seed, glane, CH);
             __syncwarp(gmask);
-            if (glane == 0) fisher_yates(perm, words, r);
+            if (glane == 0) fisher_yates(perm, reinterpret_cast<const uint8_t *>(words), r);
             __syncwarp(gmask);
         }
         group_sync();
@@ -3030,9 +3030,9 @@ __global__ void debug_perm_kernel(const int64_t *cols, int64_t count, int r, int
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * 8 + w;
     if (c >= count) return;
-    ids_words_warp(words[w], r, cols[c], sweep, side, perm_mode, seed, lane);
+    ids_swaps_warp(reinterpret_cast<uint8_t *>(words[w]), r, cols[c], sweep, side, perm_mode, seed, lane);
     __syncwarp();
-    if (lane == 0) fisher_yates(perm[w], words[w], r);
+    if (lane == 0) fisher_yates(perm[w], reinterpret_cast<const uint8_t *>(words[w]), r);
     __syncwarp();
     for (int t = lane; t < r; t += 32) out[c * r + t] = perm[w][t];
 }
